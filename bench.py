@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the FastDOG dual hot path on one GB300 (or N replicas).
+
+One step = one complete solve of the workload resident in HBM, through the
+C ABI: re-initialise the multipliers (Alg. 1 initialisation), dual
+iterations (forward / backward sweeps, deferred averaging, lower bound) until
+the 1e-4 relative stopping rule or the iteration cap, the final add-back, the
+perturbation rounding loop (Alg. 2) and the objective of the rounded point.
+
+Metric: BDD arc-updates per second = 4 x (BDD nodes) x (dual iterations run,
+including the rounding rounds' re-optimisation), over the device-timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fastdog|reference]
+
+N > 1 runs one independent replica per GPU (the single-instance path has no
+data-parallel split without a cross-GPU exchange), so scaling
+is weak and the value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # large MRF: 512 x 512 4-connected grid, 4 labels, one-hot / marginalisation encoding
+    "mrf512": dict(h=512, w=512, labels=4, seed=1, potts_max=2.0, max_iters=500,
+                   desc="MRF grid 512x512, 4 labels, Potts U(0,2), unary N(0,1), seed 1"),
+    # small case (the parity-test size)
+    "mrf8": dict(h=8, w=8, labels=3, seed=0, potts_max=1.0, max_iters=200,
+                 desc="MRF grid 8x8, 3 labels, Potts U(0,1), unary N(0,1), seed 0"),
+}
+METRIC = "BDD arc-updates/s (full FastDOG solve: dual sweeps to the 1e-4 LB gap + perturbation rounding)"
+UNIT = "arc-updates/s"
+SWEEP_SRC = os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", "sweep.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fastdog", choices=["fastdog", "reference"])
+    ap.add_argument("--workload", default="mrf512", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-iters", type=int, default=None, help="override the workload's iteration cap")
+    ap.add_argument("--dual-only", action="store_true", help="steps without rounding (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(name):
+    import ilpgen
+
+    w = WORKLOADS[name]
+    return ilpgen.mrf_grid(w["h"], w["w"], w["labels"], w["seed"], potts_max=w["potts_max"]), w
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else f"GPU-{u}"
+    except Exception:
+        return os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+
+
+# ----------------------------------------------------------------------------
+# the oracle (CPU baseline and reference arm)
+# ----------------------------------------------------------------------------
+def oracle_rate(g, iters_per_sample, samples):
+    """Arc-updates/s of the FP64 oracle: `samples` timed samples of
+    `iters_per_sample` dual iterations each on the full instance (the oracle's
+    one-off BDD construction is not timed)."""
+    import oracle
+
+    oracle.build()
+    p = oracle.Problem.from_ilp(g)
+    arcs = 4 * p.N
+    p.iterate(1)  # first pass also builds the shortest-path labels
+    rates = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        p.iterate(iters_per_sample)
+        dt = time.perf_counter() - t0
+        rates.append(arcs * iters_per_sample / dt)
+    return rates, p.N
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    g, w = make_workload(args.workload)
+    n_steps = args.steps
+    rates, nodes = oracle_rate(g, 1, args.warmup + n_steps)
+    timed = rates[args.warmup:]
+    value = len(timed) / sum(1.0 / r for r in timed)  # equal work per step: harmonic mean = total / total time
+    ms = 4 * nodes / value * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": n_steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "step": "one FP64 oracle dual iteration on the full instance"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n_steps} single dual iterations of the full {args.workload} instance "
+                                   f"(single-threaded C, FP64); BDD construction not timed"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# the CUDA path
+# ----------------------------------------------------------------------------
+def solve(inst, max_iters, kr, dual_only=False):
+    inst.reset()
+    iters, lb = inst.iterate(max_iters)
+    if dual_only:
+        return {"iters": iters, "rounds": 0, "lb": lb, "obj": None, "feasible": None, "rc": 0, "dual_iters": iters}
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    return {"iters": iters, "rounds": rounds, "lb": lb, "obj": obj, "feasible": feas, "rc": rc,
+            "dual_iters": iters + rounds * kr}
+
+
+def sweep_traffic():
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        sha = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()
+        if rec.get("sweep_source_sha256") == sha:
+            return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = local
+    import paper_2111_10270_gb300 as P
+    from paper_2111_10270_gb300 import build as libbuild
+
+    libbuild.build()
+    g, w = make_workload(args.workload)
+    w = dict(w)
+    if args.max_iters is not None:
+        w["max_iters"] = args.max_iters
+    params = P.capi.default_params(tol=1e-4)
+    kr = params.rounding_dual_iters
+    stream = torch.cuda.current_stream()
+    inst = P.Instance.from_ilp(g, params).build(dev, stream)
+    info = inst.info()
+    nodes = info["n_nodes"]
+
+    for _ in range(args.warmup):
+        solve(inst, w["max_iters"], kr, args.dual_only)
+
+    # ---- device-timed steps -------------------------------------------------
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sampler = ClockSampler(gpu_smi_id(torch, dev))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    inst.profile_read()  # clear
+    launches0 = inst.profile_read()["kernel_launches"]
+    inst.set_profiling(True)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [solve(inst, w["max_iters"], kr, args.dual_only) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    inst.set_profiling(False)
+    prof = inst.profile_read()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    dual_iters = sum(r["dual_iters"] for r in results)
+    arcs = 4.0 * nodes * dual_iters
+    if world > 1:
+        t = torch.tensor([elapsed, arcs], dtype=torch.float64, device=f"cuda:{dev}")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        elapsed, arcs = float(tmax[0]), float(t[1])
+    value = arcs / elapsed
+
+    # ---- roofline of the dominant kernel (update sweep) ----------------------
+    S = info["n_slots"]
+    n_bdds = info["n_bdds"]
+    tiles = -(-n_bdds // 32)
+    alg_bytes = 16 * S + 24 * tiles  # per sweep launch: lambda r+w, var, deferred term gather; tile header + bound
+    sweep_avg_s = prof["sweep_ms"] / max(prof["sweep_launches"], 1) / 1e3
+    reduce_avg_s = prof["reduce_ms"] / max(prof["reduce_launches"], 1) / 1e3
+    achieved = alg_bytes / sweep_avg_s / 1e9 if sweep_avg_s > 0 else None
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    if not peak:
+        peak = 6800.0
+    reduce_bytes = 8 * S + 12 * g.n_vars + 4  # per launch: slot index + gathered lambda; offsets, target, result
+    roofline = {"bound": "hbm", "kernel": "sweep_kernel<W=2,reg,update>", "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                "traffic": sweep_traffic(), "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_us": sweep_avg_s * 1e6, "launches": prof["sweep_launches"],
+                "deferred_sum_kernel": {"avg_launch_us": reduce_avg_s * 1e6, "alg_bytes_per_launch": reduce_bytes,
+                                        "achieved_gbs": reduce_bytes / reduce_avg_s / 1e9 if reduce_avg_s else None}}
+    launches = prof["kernel_launches"] - launches0
+
+    # ---- end to end through the public API from host buffers ------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_arcs, h2d, d2h = 0.0, 0, 0
+        for _ in range(args.e2e_steps):
+            e_inst = P.Instance.from_ilp(g, params).build(dev, stream)
+            r = solve(e_inst, w["max_iters"], kr, args.dual_only)
+            hb, db = e_inst.transfer_bytes()
+            h2d += hb
+            d2h += db
+            e_arcs += 4.0 * nodes * r["dual_iters"]
+            e_inst.close()
+        torch.cuda.synchronize()
+        e_t = time.perf_counter() - t0
+        e2e = {"value": e_arcs / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
+               "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "scope": "fdog_create from host CSR + host BDD planning + upload + solve + solution read-back"}
+
+    # ---- CPU baseline (rank 0, N = 1) ------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rates, _ = oracle_rate(g, 1, 6 if args.workload == "mrf512" else 20)
+        cpu = {"value": float(np.median(rates)), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"median of {len(rates)} single dual iterations of the full {args.workload} instance "
+                         f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
+
+    if rank == 0:
+        last = results[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["desc"], "vars": info["n_vars"], "bdds": n_bdds, "slots": S, "nodes": nodes,
+                       "dual_iters_per_step": dual_iters / args.steps, "stop_iters": last["iters"],
+                       "rounds": last["rounds"], "lb": last["lb"], "ub": last["obj"], "feasible": last["feasible"],
+                       "l2": "inputs larger than L2 (about 590 MB resident per instance)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    inst.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,274 @@
+/*
+ * fastdog.h -- C ABI of the GB300 FastDOG dual hot path.
+ *
+ * FastDOG (Abbas & Swoboda, CVPR 2022) solves 0-1 integer linear programs
+ *     min c^T x   s.t.  L_j <= a_j^T x <= U_j  (one row per constraint),  x in {0,1}^n
+ * by a Lagrange decomposition with one binary decision diagram (BDD) per row
+ * (Def. 1 "Binary Program", Ex. 1 "ILP", Def. 4 "BDD").  This library builds
+ * the BDDs on the host, keeps the whole dual state resident on one GPU, and
+ * runs every step of the method in hand-written sm_103a CUDA kernels:
+ *
+ *   forward / backward min-plus shortest-path sweeps     (Alg. 3, Alg. 4)
+ *   min-marginal differences M_ij = m^1_ij - m^0_ij       (Eq. MM, Eq. MD, Eq. 6)
+ *   parallel deferred min-marginal averaging, damping w   (Alg. 1, Eq. 5)
+ *   the lower bound sum_j E^j(lambda^j)                   (Eq. D, Prop. 1)
+ *   perturbation primal rounding                          (Alg. 2)
+ *
+ * Conventions (all entry points)
+ *   - Every function returns an int status: FDOG_OK (0) or a negative code
+ *     below.  No C++ exception, abort() or exit() crosses this boundary.
+ *   - Pointers named host_* / plain arrays are HOST memory unless the
+ *     parameter name says "dev".  Inputs are copied; the caller keeps
+ *     ownership of every array it passes.  Output arrays are caller-allocated.
+ *   - An instance is not thread-safe; distinct instances are independent.
+ *   - A `cuda_stream` argument is a cudaStream_t passed as void*; NULL means
+ *     the legacy default stream.  All device work of an instance is ordered on
+ *     the stream given to fdog_build_bdds.
+ *   - Floating point: sweeps, multipliers and min-marginals are FP32; lower
+ *     bounds and objectives are reduced in FP64 with compensated summation.
+ */
+#ifndef FASTDOG_H
+#define FASTDOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define FDOG_OK 0
+#define FDOG_EINVAL (-1)        /* malformed input (CSR, sense, coefficient, parameter, NULL pointer) */
+#define FDOG_ENOMEM (-2)        /* host or device allocation failed, or a row's BDD is too large */
+#define FDOG_EINFEASIBLE (-3)   /* some row (after presolve) has an empty feasible set */
+#define FDOG_ECUDA (-4)         /* a CUDA runtime call or kernel launch failed */
+#define FDOG_ESTATE (-5)        /* call out of order (e.g. iterate before fdog_build_bdds) */
+#define FDOG_ETIMEOUT (-6)      /* a bounded device-side wait expired; the context stays usable */
+#define FDOG_ENOCONVERGE (-7)   /* rounding hit max_rounds; a solution is still returned, feasible=0 */
+#define FDOG_EUNSUPPORTED (-8)  /* valid request this build does not handle */
+
+/* row sense: a_j^T x <= b_j, == b_j, >= b_j */
+#define FDOG_LE (-1)
+#define FDOG_EQ 0
+#define FDOG_GE 1
+
+typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
+
+/*
+ * Parameters.  Defaults (fdog_params_default):
+ *   omega = 0.5      damping of the deferred averaging, must lie in (0, 1]
+ *                    (Alg. 1 input; 0.5 in the paper's experiments, Sec. 3.3)
+ *   delta = 1.0      initial perturbation strength of Alg. 2 (Sec. 6)
+ *   alpha = 1.2      perturbation growth rate of Alg. 2 (Sec. 6)
+ *   tol   = 1e-4     stopping rule: stop once
+ *                    LB_t - LB_{t-window} <= tol * max(|LB_t|, 1)
+ *                    after at least min_iters iterations (the paper stops on
+ *                    the relative change of the dual objective, Sec. 3.3);
+ *                    tol <= 0 disables early stopping
+ *   window = 10, min_iters = 20
+ *   rounding_dual_iters = 20   Alg. 1 iterations per rounding round (Alg. 2
+ *                              "reoptimize"; the count is not stated)
+ *   max_rounds = 200           cap on Alg. 2 rounds (termination is not
+ *                              guaranteed, Sec. 4)
+ *   seed = 0                   seed of the counter-based perturbation draws
+ *   block_threads = 0          threads per CTA for the sweep kernels;
+ *                              0 = use the built-in autotuner
+ */
+typedef struct {
+    double omega;
+    double delta;
+    double alpha;
+    double tol;
+    int32_t window;
+    int32_t min_iters;
+    int32_t rounding_dual_iters;
+    int32_t max_rounds;
+    uint64_t seed;
+    int32_t block_threads;
+    int32_t reserved[7];
+} fdog_params;
+
+/* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */
+int fdog_params_default(fdog_params* p);
+
+/*
+ * Create an instance from a sparse 0-1 ILP (Ex. 1).  Row j has entries
+ * col[row_ptr[j] .. row_ptr[j+1]) with integer coefficients coef[...],
+ * sense[j] in {FDOG_LE, FDOG_EQ, FDOG_GE} and integer right-hand side rhs[j].
+ * cost has n_vars finite entries.  All arrays are host memory and are copied.
+ * Errors: FDOG_EINVAL for a negative size, a decreasing row_ptr, a column
+ * out of [0, n_vars), a repeated column within a row, a bad sense, a
+ * non-finite cost or invalid params; FDOG_ENOMEM.  params may be NULL
+ * (defaults).  On success *out owns the instance (free with fdog_destroy).
+ */
+int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                const int32_t* coef, const int8_t* sense, const int64_t* rhs, const fdog_params* params,
+                fdog_instance** out);
+
+/*
+ * Host-only planning: presolve, BDD construction and the device layout,
+ * without touching a GPU.  *device_bytes (may be NULL) receives the device
+ * memory fdog_build_bdds will allocate (what an admission controller needs).
+ * Calling it is optional; fdog_build_bdds plans if needed.  Same errors as
+ * fdog_build_bdds minus FDOG_ECUDA.
+ */
+int fdog_plan(fdog_instance* inst, int64_t* device_bytes);
+
+/*
+ * Introspection of a planned instance.  fdog_fixed_vars writes n_vars bytes:
+ * -1 for a variable inside some BDD, 0 / 1 for a variable fixed by presolve,
+ * 2 for a variable in no remaining row.  fdog_row_bdd exports the BDD of
+ * original row `row` (Def. 4): *k layers over variables vars[0..k) in
+ * ascending order, *n_nodes nodes, layer t = nodes [lstart[t], lstart[t+1]),
+ * node 0 the root, lo/hi the 0-/1-arc successors as node indices or -1 (TOP)
+ * / -2 (BOT).  Pass NULL arrays to query *k and *n_nodes; a row removed by
+ * presolve gives *k = 0.  FDOG_ESTATE if not planned.
+ */
+int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed);
+int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes, int32_t* vars, int32_t* lstart,
+                 int32_t* lo, int32_t* hi);
+
+/*
+ * Build the decomposition and upload it to `device` on `cuda_stream`:
+ * presolve (fix variables a row forces, drop rows every assignment
+ * satisfies), one reduced ordered BDD per remaining row over its variables in
+ * ascending index order (Def. 4; arcs leaving layer i carry lambda_i as in
+ * Fig. 3), the node layout, and the initial multipliers
+ * lambda^j_i = c_i / |J_i| with M-bar = 0 (Alg. 1 text).
+ * Errors: FDOG_EINFEASIBLE (a row cannot be satisfied), FDOG_ENOMEM (host or
+ * device memory, or a row whose BDD exceeds the node limit), FDOG_ECUDA,
+ * FDOG_ESTATE if already built.  May be called once per instance.
+ */
+int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream);
+
+/*
+ * Re-initialise the dual state on the device: lambda^j_i = c_i / |J_i|,
+ * M-bar = 0, iteration counter and stopping history cleared (Alg. 1
+ * initialisation).  The decomposition stays resident.
+ */
+int fdog_reset_dual(fdog_instance* inst);
+
+/*
+ * Run up to k iterations of Alg. 1 (one ascending and one descending pass
+ * each, Eq. 5 updates, deferred sums refreshed after every pass), stopping
+ * early when the stopping rule of fdog_params holds.  The deferred
+ * differences of the last pass stay pending (see fdog_lower_bound).
+ * *iters_done (may be NULL) receives the iterations run by this call and *lb
+ * (may be NULL) the running lower bound after the last one.  Blocks until the
+ * device work is done.  Errors: FDOG_ESTATE (not built), FDOG_EINVAL (k < 0),
+ * FDOG_ECUDA.
+ */
+int fdog_dual_iterate(fdog_instance* inst, int32_t k, int32_t* iters_done, double* lb);
+
+/*
+ * Final loop of Alg. 1: add the pending deferred differences back,
+ * lambda^j_i += omega / |J_i| sum_k Mbar_ik, so that sum_j lambda^j_i = c_i
+ * again (dual feasibility, Prop. 1).  No-op if nothing is pending.  A later
+ * fdog_dual_iterate restarts Alg. 1 from M-bar = 0.
+ */
+int fdog_finalize(fdog_instance* inst);
+
+/*
+ * Lower bounds at the current state, both valid for the ILP (Prop. 1):
+ *   *lb_running  = sum_j E^j of the lifted multipliers (the bound the
+ *                  iterations report; non-decreasing),
+ *   *lb_feasible = sum_j E^j(lambda^j) after adding the pending deferred
+ *                  differences back (Alg. 1, last loop), i.e. at dual-feasible
+ *                  multipliers with sum_j lambda^j_i = c_i.
+ * Both include the constant of variables fixed by presolve or in no row.
+ * Either pointer may be NULL.  Does not modify the state.
+ */
+int fdog_lower_bound(fdog_instance* inst, double* lb_running, double* lb_feasible);
+
+/*
+ * Min-marginals (Eq. MM) of every (row, variable) slot at the current
+ * multipliers lambda (pending deferred differences NOT added), computed on
+ * the GPU by Eq. 6.  If var == NULL the call only stores the slot count in
+ * *n_slots.  Otherwise *n_slots must hold the capacity of the four arrays;
+ * slot s is (row[s], var[s]) with min-marginals m0[s], m1[s]; rows are the
+ * caller's original row indices.  FDOG_EINVAL if the capacity is too small.
+ */
+int fdog_min_marginals(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_t* row, float* m0, float* m1);
+
+/*
+ * Current multipliers lambda^j_i of every slot (same slot order and size
+ * query convention as fdog_min_marginals).  lambda may be NULL.
+ */
+int fdog_multipliers(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_t* row, float* lambda);
+
+/*
+ * Perturbation primal rounding (Alg. 2): add the pending deferred
+ * differences back, compute all M_ij, and while some variable's M_ij do not
+ * all share one strict sign, perturb every variable by the four cases of
+ * Alg. 2 (r uniform in [-1, 1) from SplitMix64(seed ^ round<<32 ^ i)), grow
+ * delta by alpha, re-run rounding_dual_iters iterations of Alg. 1 and the
+ * add-back, and recompute M.  At agreement x_i = [M_ij < 0].
+ * *rounds_used (may be NULL) receives the number of perturbation rounds.
+ * Returns FDOG_ENOCONVERGE after max_rounds rounds without agreement (the
+ * solution is then x_i = [sum_j M_ij < 0], possibly infeasible).
+ * The multipliers are left perturbed (Alg. 2 does not keep them feasible).
+ */
+int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used);
+
+/*
+ * The last rounded solution: x (n_vars bytes, may be NULL), its objective
+ * c^T x summed in FP64 (may be NULL), and *feasible = 1 iff x satisfies every
+ * row exactly (integer check on the host; may be NULL).
+ * FDOG_ESTATE if fdog_primal_round has not run.
+ */
+int fdog_solution(fdog_instance* inst, uint8_t* x, double* objective, int32_t* feasible);
+
+/*
+ * Checkpoint: the complete resumable dual state (multipliers, deferred sums,
+ * per-variable targets, iteration count, stopping history).  If buf is NULL,
+ * *bytes receives the size.  fdog_import_state restores a state exported
+ * from an instance built from the same ILP and parameters; a resumed run is
+ * bit-identical to an uninterrupted one.  FDOG_EINVAL on a size or
+ * signature mismatch.
+ */
+int fdog_export_state(fdog_instance* inst, void* buf, size_t* bytes);
+int fdog_import_state(fdog_instance* inst, const void* buf, size_t bytes);
+
+/*
+ * Sizes of the built decomposition (any pointer may be NULL): variables,
+ * BDDs, slots (sum_j |I_j|), BDD nodes, and device bytes held.
+ */
+int fdog_info(fdog_instance* inst, int64_t* n_vars, int64_t* n_bdds, int64_t* n_slots, int64_t* n_nodes,
+              int64_t* device_bytes);
+
+/*
+ * Bytes the library has copied host-to-device and device-to-host for this
+ * instance since it was created (uploads, control-block reads, results).
+ */
+int fdog_transfer_bytes(fdog_instance* inst, int64_t* h2d, int64_t* d2h);
+
+/*
+ * Kernel timing.  While profiling is on, every update-pass sweep launch (the
+ * ascending / descending passes of Alg. 1) and every per-variable
+ * deferred-sum launch is bracketed by CUDA events on the instance's stream.
+ * fdog_profile_read synchronises the stream and returns the launches and
+ * summed device milliseconds of both kernels recorded since the last read,
+ * plus *kernel_launches = all kernel launches of the instance since it was
+ * built (always counted).  Any output pointer may be NULL.
+ */
+int fdog_set_profiling(fdog_instance* inst, int32_t on);
+int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* sweep_ms, int64_t* reduce_launches,
+                      double* reduce_ms, int64_t* kernel_launches);
+
+/*
+ * Human-readable detail of the last error status returned for this instance
+ * (empty if none).  The pointer stays valid until the next call on inst.
+ */
+const char* fdog_last_error(const fdog_instance* inst);
+
+/* Free the instance and its device memory.  NULL is accepted. */
+void fdog_destroy(fdog_instance* inst);
+
+/* Static text for a status code. */
+const char* fdog_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTDOG_H */

@@ -1,0 +1,714 @@
+// C ABI of the FastDOG GB300 library (include/fastdog.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "instance.h"
+#include "kernels.h"
+
+using namespace fdog;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+namespace fdog {
+
+cudaError_t copy_async(fdog_instance* inst, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+    if (kind == cudaMemcpyHostToDevice) inst->h2d_bytes += static_cast<int64_t>(bytes);
+    if (kind == cudaMemcpyDeviceToHost) inst->d2h_bytes += static_cast<int64_t>(bytes);
+    return cudaMemcpyAsync(dst, src, bytes, kind, inst->stream);
+}
+
+int fail_cuda(fdog_instance* inst, cudaError_t e, const char* where) {
+    if (inst) inst->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return FDOG_ECUDA;
+}
+
+struct Item {
+    void** ptr;
+    size_t bytes;
+};
+
+// Every device array of the instance, in arena order.
+static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
+    const Decomposition& d = inst->dec;
+    const int64_t n = inst->n_vars;
+    const int64_t S = d.slots_pad;
+    const int64_t nt = static_cast<int64_t>(d.tiles.size());
+    const int64_t nchunks = std::max<int64_t>(1, (nt + kLbChunk - 1) / kLbChunk);
+    const int64_t nobj = std::max<int64_t>(1, (n + kObjChunk - 1) / kObjChunk);
+    auto sz = [](int64_t v) { return static_cast<size_t>(std::max<int64_t>(v, 1)); };
+    return {
+        {reinterpret_cast<void**>(&a.inst), sizeof(InstDev)},
+        {reinterpret_cast<void**>(&a.ctl), sizeof(InstCtl)},
+        {reinterpret_cast<void**>(&a.tiles), sizeof(TileDev) * sz(nt)},
+        {reinterpret_cast<void**>(&a.shapes), sizeof(ShapeDev) * sz(static_cast<int64_t>(d.shape_dev.size()))},
+        {reinterpret_cast<void**>(&a.tpl), sizeof(uint16_t) * std::max<size_t>(d.tpl.size(), 8)},
+        {reinterpret_cast<void**>(&a.lam), sizeof(float) * sz(S)},
+        {reinterpret_cast<void**>(&a.var), sizeof(int32_t) * sz(S)},
+        {reinterpret_cast<void**>(&a.mm0), sizeof(float) * sz(S)},
+        {reinterpret_cast<void**>(&a.T), sizeof(float) * sz(n)},
+        {reinterpret_cast<void**>(&a.C), sizeof(float) * sz(n)},
+        {reinterpret_cast<void**>(&a.pert), sizeof(float) * sz(n)},
+        {reinterpret_cast<void**>(&a.x), sz(n)},
+        {reinterpret_cast<void**>(&a.cost), sizeof(double) * sz(n)},
+        {reinterpret_cast<void**>(&a.csr_off), sizeof(int32_t) * static_cast<size_t>(n + 1)},
+        {reinterpret_cast<void**>(&a.csr_pos), sizeof(int32_t) * sz(d.n_slots)},
+        {reinterpret_cast<void**>(&a.tile_lb), sizeof(double) * sz(nt)},
+        {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
+        {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
+        {reinterpret_cast<void**>(&a.prefix), sizeof(int32_t) * kPrefixInts},
+    };
+}
+
+size_t arena_size(const fdog_instance* inst) {
+    DevArrays tmp;
+    size_t total = 0;
+    for (const Item& it : arena_items(inst, tmp)) total = align_up(total + it.bytes, 256);
+    return total;
+}
+
+int plan(fdog_instance* inst) {
+    if (inst->planned) return FDOG_OK;
+    int rc;
+    try {
+        rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
+                                 inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(), inst->dec,
+                                 inst->last_error);
+    } catch (const std::bad_alloc&) {
+        rc = FDOG_ENOMEM;
+    } catch (...) {
+        rc = FDOG_EINVAL;
+    }
+    if (rc != FDOG_OK) return rc;
+    for (int c = 0; c < kNumClasses; ++c)
+        if (!class_is_reg(c) && inst->dec.kmax[c] > smem_max_layers(class_width(c))) {
+            inst->last_error = "row longer than the shared-memory sweep kernels take";
+            return FDOG_EUNSUPPORTED;
+        }
+    inst->planned = true;
+    return FDOG_OK;
+}
+
+// Lay out every device array of the instance inside one allocation.
+int allocate_and_upload(fdog_instance* inst) {
+    Decomposition& d = inst->dec;
+    const int64_t n = inst->n_vars;
+    const int64_t S = d.slots_pad;
+    const int64_t nt = static_cast<int64_t>(d.tiles.size());
+    const int64_t nchunks = std::max<int64_t>(1, (nt + kLbChunk - 1) / kLbChunk);
+    const int64_t nobj = std::max<int64_t>(1, (n + kObjChunk - 1) / kObjChunk);
+    DevArrays& a = inst->dev;
+    std::vector<Item> items = arena_items(inst, a);
+    size_t total = 0;
+    std::vector<size_t> offs(items.size());
+    for (size_t q = 0; q < items.size(); ++q) {
+        offs[q] = total;
+        total = align_up(total + items[q].bytes, 256);
+    }
+    cudaError_t e = cudaMalloc(&inst->arena, total);
+    if (e != cudaSuccess) {
+        inst->arena = nullptr;
+        inst->last_error = "cudaMalloc of " + std::to_string(total) + " bytes failed";
+        cudaGetLastError();
+        return FDOG_ENOMEM;
+    }
+    inst->arena_bytes = total;
+    for (size_t q = 0; q < items.size(); ++q) *items[q].ptr = static_cast<char*>(inst->arena) + offs[q];
+
+    // descriptor
+    InstDev h{};
+    h.tiles = a.tiles;
+    h.shapes = a.shapes;
+    h.tpl = a.tpl;
+    h.lam = a.lam;
+    h.var = a.var;
+    h.mm0 = a.mm0;
+    h.mm1 = nullptr;
+    h.T = a.T;
+    h.C = a.C;
+    h.csr_off = a.csr_off;
+    h.csr_pos = a.csr_pos;
+    h.cost = a.cost;
+    h.pert = a.pert;
+    h.x = a.x;
+    h.tile_lb = a.tile_lb;
+    h.chunk_lb = a.chunk_lb;
+    h.obj_chunk = a.obj_chunk;
+    h.ctl = a.ctl;
+    h.n_tiles = static_cast<int32_t>(nt);
+    h.n_vars = static_cast<int32_t>(n);
+    h.n_chunks = static_cast<int32_t>(nchunks);
+    h.n_obj_chunks = static_cast<int32_t>(nobj);
+    h.omega = static_cast<float>(inst->params.omega);
+    h.const_lb = d.const_lb;
+    inst->hdesc = h;
+
+    // self-batch prefix arrays: per class (prefix[2], first[1]), then vars, slots, chunks, objective chunks
+    std::vector<int32_t> pre(kPrefixInts, 0);
+    DevBatch& b = inst->batch;
+    b = DevBatch();
+    b.insts = a.inst;
+    b.n_inst = 1;
+    int q = 0;
+    for (int c = 0; c < kNumClasses; ++c) {
+        pre[q] = 0;
+        pre[q + 1] = d.cls_tile_begin[c + 1] - d.cls_tile_begin[c];
+        pre[q + 2] = d.cls_tile_begin[c];
+        b.tile_prefix[c] = a.prefix + q;
+        b.tile_first[c] = a.prefix + q + 2;
+        b.tiles_total[c] = pre[q + 1];
+        b.kmax[c] = d.kmax[c];
+        q += 3;
+    }
+    auto two = [&](int32_t** dst, int32_t v) {
+        pre[q] = 0;
+        pre[q + 1] = v;
+        *dst = a.prefix + q;
+        q += 2;
+    };
+    two(&b.var_prefix, static_cast<int32_t>(n));
+    b.vars_total = static_cast<int32_t>(n);
+    two(&b.slot_prefix, static_cast<int32_t>(S));
+    b.slots_total = static_cast<int32_t>(S);
+    two(&b.chunk_prefix, static_cast<int32_t>(nt > 0 ? nchunks : 0));
+    b.chunks_total = static_cast<int32_t>(nt > 0 ? nchunks : 0);
+    two(&b.objchunk_prefix, static_cast<int32_t>(n > 0 ? nobj : 0));
+    b.objchunks_total = static_cast<int32_t>(n > 0 ? nobj : 0);
+
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes == 0 || e != cudaSuccess) return;
+        e = copy_async(inst, dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(a.inst, &h, sizeof(h));
+    up(a.tiles, d.tiles.data(), sizeof(TileDev) * nt);
+    up(a.shapes, d.shape_dev.data(), sizeof(ShapeDev) * d.shape_dev.size());
+    up(a.tpl, d.tpl.data(), sizeof(uint16_t) * d.tpl.size());
+    up(a.var, d.var.data(), sizeof(int32_t) * S);
+    up(a.cost, inst->cost.data(), sizeof(double) * n);
+    up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
+    up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
+    up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
+    return FDOG_OK;
+}
+
+int reset_dual_state(fdog_instance* inst) {
+    InstCtl c{};
+    const fdog_params& p = inst->params;
+    c.stop_enabled = p.tol > 0 ? 1 : 0;
+    c.window = p.window;
+    c.min_iters = p.min_iters;
+    c.tol = p.tol;
+    cudaError_t e = copy_async(inst, inst->dev.ctl, &c, sizeof(c), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "reset ctl");
+    e = launch_init(inst->batch, inst->cfg, inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "init");
+    inst->pending_T = false;
+    inst->iterated = false;
+    return FDOG_OK;
+}
+
+int read_ctl(fdog_instance* inst, InstCtl& out) {
+    cudaError_t e = copy_async(inst, inst->host_ctl, inst->dev.ctl, sizeof(InstCtl), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "read control block");
+    out = *inst->host_ctl;
+    if (out.error != 0) {
+        inst->last_error = "device-side error " + std::to_string(out.error);
+        return FDOG_ETIMEOUT;
+    }
+    return FDOG_OK;
+}
+
+int set_ctl_field(fdog_instance* inst, size_t offset, const void* v, size_t bytes) {
+    cudaError_t e = copy_async(inst, reinterpret_cast<char*>(inst->dev.ctl) + offset, v, bytes,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);  // v may be a stack temporary
+    return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "write control block");
+}
+
+// Energy sum (+ presolve constant) at lambda, or at lambda + T (the add-back).
+int evaluate(fdog_instance* inst, bool add_t, double* out) {
+    cudaError_t e = launch_sweep(inst->batch, kEval, add_t ? kMMAddT : 0, inst->cfg, inst->stream);
+    if (e == cudaSuccess) e = launch_lb_reduce(inst->batch, kLbEval, inst->cfg, inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "evaluate");
+    InstCtl c;
+    int rc = read_ctl(inst, c);
+    if (rc != FDOG_OK) return rc;
+    *out = inst->dec.n_bdds > 0 ? c.lb_eval : inst->dec.const_lb;
+    return FDOG_OK;
+}
+
+int addback(fdog_instance* inst) {
+    if (!inst->pending_T) return FDOG_OK;
+    cudaError_t e = launch_addback(inst->batch, inst->cfg, inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "add-back");
+    inst->pending_T = false;
+    inst->iterated = false;
+    return FDOG_OK;
+}
+
+int ensure_mm1(fdog_instance* inst) {
+    if (inst->dev.mm1) return FDOG_OK;
+    void* p = nullptr;
+    size_t bytes = sizeof(float) * std::max<int64_t>(inst->dec.slots_pad, 1);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); return FDOG_ENOMEM; }
+    inst->dev.mm1 = static_cast<float*>(p);
+    inst->hdesc.mm1 = inst->dev.mm1;
+    e = copy_async(inst, inst->dev.inst, &inst->hdesc, sizeof(InstDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);
+    return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "descriptor update");
+}
+
+}  // namespace fdog
+
+// ===========================================================================
+// extern "C"
+// ===========================================================================
+extern "C" {
+
+int fdog_params_default(fdog_params* p) {
+    if (!p) return FDOG_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->omega = 0.5;
+    p->delta = 1.0;
+    p->alpha = 1.2;
+    p->tol = 1e-4;
+    p->window = 10;
+    p->min_iters = 20;
+    p->rounding_dual_iters = 20;
+    p->max_rounds = 200;
+    p->seed = 0;
+    p->block_threads = 0;
+    return FDOG_OK;
+}
+
+const char* fdog_status_string(int s) {
+    switch (s) {
+        case FDOG_OK: return "ok";
+        case FDOG_EINVAL: return "invalid argument";
+        case FDOG_ENOMEM: return "out of memory";
+        case FDOG_EINFEASIBLE: return "infeasible row";
+        case FDOG_ECUDA: return "CUDA error";
+        case FDOG_ESTATE: return "call out of order";
+        case FDOG_ETIMEOUT: return "device wait timed out";
+        case FDOG_ENOCONVERGE: return "rounding did not converge";
+        case FDOG_EUNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr, const int32_t* col,
+                const int32_t* coef, const int8_t* sense, const int64_t* rhs, const fdog_params* params,
+                fdog_instance** out) {
+    if (!out) return FDOG_EINVAL;
+    *out = nullptr;
+    if (n_vars < 0 || n_rows < 0) return FDOG_EINVAL;
+    if ((n_vars > 0 && !cost) || (n_rows > 0 && (!row_ptr || !sense || !rhs))) return FDOG_EINVAL;
+    fdog_params p;
+    if (params) p = *params; else fdog_params_default(&p);
+    if (!(p.omega > 0.0 && p.omega <= 1.0) || !(p.delta > 0.0) || !(p.alpha >= 1.0) || p.window < 1 ||
+        p.window >= kLbRing || p.min_iters < 0 || p.rounding_dual_iters < 0 || p.max_rounds < 0 ||
+        p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0)
+        return FDOG_EINVAL;
+    for (int32_t i = 0; i < n_vars; ++i)
+        if (!std::isfinite(cost[i])) return FDOG_EINVAL;
+    if (n_rows > 0) {
+        if (row_ptr[0] != 0) return FDOG_EINVAL;
+        for (int32_t j = 0; j < n_rows; ++j) {
+            if (row_ptr[j + 1] < row_ptr[j]) return FDOG_EINVAL;
+            if (sense[j] < -1 || sense[j] > 1) return FDOG_EINVAL;
+        }
+        const int64_t nnz = row_ptr[n_rows];
+        if (nnz > 0 && (!col || !coef)) return FDOG_EINVAL;
+        std::vector<int32_t> last(n_vars, -1);
+        for (int32_t j = 0; j < n_rows; ++j)
+            for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q) {
+                if (col[q] < 0 || col[q] >= n_vars) return FDOG_EINVAL;
+                if (last[col[q]] == j) return FDOG_EINVAL;  // repeated column in a row
+                last[col[q]] = j;
+            }
+    }
+    fdog_instance* inst = new (std::nothrow) fdog_instance();
+    if (!inst) return FDOG_ENOMEM;
+    try {
+        inst->n_vars = n_vars;
+        inst->n_rows = n_rows;
+        inst->params = p;
+        inst->cost.assign(cost, cost + n_vars);
+        inst->row_ptr.assign(row_ptr, row_ptr + (n_rows > 0 ? n_rows + 1 : 0));
+        if (inst->row_ptr.empty()) inst->row_ptr.push_back(0);
+        const int64_t nnz = inst->row_ptr.back();
+        inst->col.assign(col, col + nnz);
+        inst->coef.assign(coef, coef + nnz);
+        inst->sense.assign(sense, sense + n_rows);
+        inst->rhs.assign(rhs, rhs + n_rows);
+    } catch (...) {
+        delete inst;
+        return FDOG_ENOMEM;
+    }
+    *out = inst;
+    return FDOG_OK;
+}
+
+int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream) {
+    if (!inst) return FDOG_EINVAL;
+    if (inst->built) return FDOG_ESTATE;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        inst->last_error = "no CUDA device " + std::to_string(device);
+        return e != cudaSuccess ? FDOG_ECUDA : FDOG_EINVAL;
+    }
+    DeviceGuard g(device);
+    inst->device = device;
+    inst->stream = static_cast<cudaStream_t>(cuda_stream);
+    int rc = plan(inst);
+    if (rc != FDOG_OK) return rc;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "device properties");
+    inst->cfg.num_sms = prop.multiProcessorCount;
+    inst->cfg.warps_per_block = inst->params.block_threads > 0 ? inst->params.block_threads / 32 : 4;
+    inst->cfg.prof = &inst->prof;
+    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_ctl), sizeof(InstCtl));
+    if (e != cudaSuccess) { cudaGetLastError(); inst->host_ctl = nullptr; return FDOG_ENOMEM; }
+    rc = allocate_and_upload(inst);
+    if (rc != FDOG_OK) return rc;
+    rc = reset_dual_state(inst);
+    if (rc != FDOG_OK) return rc;
+    e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "build");
+    inst->built = true;
+    return FDOG_OK;
+}
+
+int fdog_plan(fdog_instance* inst, int64_t* device_bytes) {
+    if (!inst) return FDOG_EINVAL;
+    int rc = plan(inst);
+    if (rc != FDOG_OK) return rc;
+    if (device_bytes) *device_bytes = static_cast<int64_t>(arena_size(inst));
+    return FDOG_OK;
+}
+
+int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed) {
+    if (!inst || !fixed) return FDOG_EINVAL;
+    if (!inst->planned) return FDOG_ESTATE;
+    std::memcpy(fixed, inst->dec.fixed.data(), inst->dec.fixed.size());
+    return FDOG_OK;
+}
+
+int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes, int32_t* vars, int32_t* lstart,
+                 int32_t* lo, int32_t* hi) {
+    if (!inst || !k || !n_nodes || row < 0 || row >= inst->n_rows) return FDOG_EINVAL;
+    if (!inst->planned) return FDOG_ESTATE;
+    const Decomposition& d = inst->dec;
+    const int32_t b = d.row_bdd[row];
+    if (b < 0) { *k = 0; *n_nodes = 0; return FDOG_OK; }
+    const HostShape& sh = d.shapes[d.bdd_shape[b]];
+    *k = sh.k;
+    *n_nodes = static_cast<int32_t>(sh.lo.size());
+    if (vars)
+        for (int t = 0; t < sh.k; ++t) vars[t] = d.var[d.bdd_slot0[b] + static_cast<int64_t>(t) * kTile];
+    if (lstart) std::copy(sh.lstart.begin(), sh.lstart.end(), lstart);
+    if (lo) std::copy(sh.lo.begin(), sh.lo.end(), lo);
+    if (hi) std::copy(sh.hi.begin(), sh.hi.end(), hi);
+    return FDOG_OK;
+}
+
+int fdog_reset_dual(fdog_instance* inst) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    int rc = reset_dual_state(inst);
+    if (rc != FDOG_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(inst->stream);
+    return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "reset");
+}
+
+int fdog_transfer_bytes(fdog_instance* inst, int64_t* h2d, int64_t* d2h) {
+    if (!inst) return FDOG_EINVAL;
+    if (h2d) *h2d = inst->h2d_bytes;
+    if (d2h) *d2h = inst->d2h_bytes;
+    return FDOG_OK;
+}
+
+int fdog_set_profiling(fdog_instance* inst, int32_t on) {
+    if (!inst) return FDOG_EINVAL;
+    inst->prof.on = on != 0;
+    return FDOG_OK;
+}
+
+int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* sweep_ms, int64_t* reduce_launches,
+                      double* reduce_ms, int64_t* kernel_launches) {
+    if (kernel_launches) *kernel_launches = inst ? inst->prof.launches : 0;
+    if (!inst) return FDOG_EINVAL;
+    int64_t ns = 0, nr = 0;
+    double ms = 0.0, mr = 0.0;
+    if (inst->built) {
+        DeviceGuard g(inst->device);
+        cudaError_t e = cudaStreamSynchronize(inst->stream);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "profile");
+        inst->prof.drain(ns, ms, nr, mr);
+    }
+    if (sweep_launches) *sweep_launches = ns;
+    if (sweep_ms) *sweep_ms = ms;
+    if (reduce_launches) *reduce_launches = nr;
+    if (reduce_ms) *reduce_ms = mr;
+    return FDOG_OK;
+}
+
+int fdog_dual_iterate(fdog_instance* inst, int32_t k, int32_t* iters_done, double* lb) {
+    if (!inst || k < 0) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    InstCtl before;
+    int rc = read_ctl(inst, before);
+    if (rc != FDOG_OK) return rc;
+    if (inst->dec.n_bdds > 0) {
+        for (int32_t t = 0; t < k; ++t) {
+            cudaError_t e = launch_iteration(inst->batch, inst->cfg, inst->stream);
+            if (e != cudaSuccess) return fail_cuda(inst, e, "iteration");
+        }
+    }
+    InstCtl after;
+    rc = read_ctl(inst, after);
+    if (rc != FDOG_OK) return rc;
+    const int32_t done = after.iter - before.iter;
+    if (done > 0) { inst->pending_T = true; inst->iterated = true; }
+    if (iters_done) *iters_done = done;
+    if (lb) {
+        if (inst->dec.n_bdds == 0) *lb = inst->dec.const_lb;
+        else if (inst->iterated) *lb = after.lb_last;
+        else return fdog_lower_bound(inst, lb, nullptr);
+    }
+    return FDOG_OK;
+}
+
+int fdog_finalize(fdog_instance* inst) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    int rc = addback(inst);
+    if (rc != FDOG_OK) return rc;
+    cudaError_t e = cudaStreamSynchronize(inst->stream);
+    return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "finalize");
+}
+
+int fdog_lower_bound(fdog_instance* inst, double* lb_running, double* lb_feasible) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    int rc;
+    if (lb_running) {
+        if (inst->iterated && inst->dec.n_bdds > 0) {
+            InstCtl c;
+            if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
+            *lb_running = c.lb_last;
+        } else if ((rc = evaluate(inst, false, lb_running)) != FDOG_OK) {
+            return rc;
+        }
+    }
+    if (lb_feasible && (rc = evaluate(inst, inst->pending_T, lb_feasible)) != FDOG_OK) return rc;
+    return FDOG_OK;
+}
+
+static int slot_table(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_t* row) {
+    const Decomposition& d = inst->dec;
+    if (!var) { *n_slots = d.n_slots; return FDOG_OK; }
+    if (*n_slots < d.n_slots) return FDOG_EINVAL;
+    int64_t q = 0;
+    for (const TileDev& t : d.tiles) {
+        const int k = d.shapes[t.shape].k;
+        for (int l = 0; l < t.n_valid; ++l)
+            for (int layer = 0; layer < k; ++layer) {
+                const int64_t p = t.slot_base + static_cast<int64_t>(layer) * kTile + l;
+                var[q] = d.var[p];
+                if (row) row[q] = d.bdd_row[t.bdd_base + l];
+                ++q;
+            }
+    }
+    *n_slots = q;
+    return FDOG_OK;
+}
+
+static int gather_slots(fdog_instance* inst, const float* dev, float* out) {
+    const Decomposition& d = inst->dec;
+    std::vector<float> h(d.slots_pad);
+    cudaError_t e = copy_async(inst, h.data(), dev, sizeof(float) * d.slots_pad, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "copy slots");
+    int64_t q = 0;
+    for (const TileDev& t : d.tiles) {
+        const int k = d.shapes[t.shape].k;
+        for (int l = 0; l < t.n_valid; ++l)
+            for (int layer = 0; layer < k; ++layer) out[q++] = h[t.slot_base + static_cast<int64_t>(layer) * kTile + l];
+    }
+    return FDOG_OK;
+}
+
+int fdog_min_marginals(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_t* row, float* m0, float* m1) {
+    if (!inst || !n_slots) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    if (!var) return slot_table(inst, n_slots, nullptr, nullptr);
+    if (*n_slots < inst->dec.n_slots) return FDOG_EINVAL;
+    DeviceGuard g(inst->device);
+    int rc = ensure_mm1(inst);
+    if (rc != FDOG_OK) return rc;
+    if (inst->dec.n_bdds > 0) {
+        cudaError_t e = launch_sweep(inst->batch, kMinMarg, kMMBoth, inst->cfg, inst->stream);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "min-marginals");
+    }
+    if ((rc = slot_table(inst, n_slots, var, row)) != FDOG_OK) return rc;
+    if (m0 && (rc = gather_slots(inst, inst->dev.mm0, m0)) != FDOG_OK) return rc;
+    if (m1 && (rc = gather_slots(inst, inst->dev.mm1, m1)) != FDOG_OK) return rc;
+    return FDOG_OK;
+}
+
+int fdog_multipliers(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_t* row, float* lambda) {
+    if (!inst || !n_slots) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    if (!var) return slot_table(inst, n_slots, nullptr, nullptr);
+    if (*n_slots < inst->dec.n_slots) return FDOG_EINVAL;
+    DeviceGuard g(inst->device);
+    int rc = slot_table(inst, n_slots, var, row);
+    if (rc == FDOG_OK && lambda) rc = gather_slots(inst, inst->dev.lam, lambda);
+    return rc;
+}
+
+int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->built) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    const fdog_params& p = inst->params;
+    cudaStream_t s = inst->stream;
+    int rc = addback(inst);
+    if (rc != FDOG_OK) return rc;
+    const int32_t zero = 0;
+    if ((rc = set_ctl_field(inst, offsetof(InstCtl, stop_enabled), &zero, sizeof(zero))) != FDOG_OK) return rc;
+    if ((rc = set_ctl_field(inst, offsetof(InstCtl, done), &zero, sizeof(zero))) != FDOG_OK) return rc;
+    double delta = p.delta;
+    int round = 0;
+    int status = FDOG_OK;
+    const bool any = inst->dec.n_bdds > 0;
+    while (any) {
+        cudaError_t e = launch_sweep(inst->batch, kMinMarg, 0, inst->cfg, s);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(reinterpret_cast<char*>(inst->dev.ctl) + offsetof(InstCtl, n_disagree), 0,
+                                sizeof(int32_t), s);
+        if (e == cudaSuccess) e = launch_round_test(inst->batch, round, delta, p.seed, inst->cfg, s);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "rounding test");
+        InstCtl c;
+        if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
+        if (c.n_disagree == 0) break;
+        if (round >= p.max_rounds) { status = FDOG_ENOCONVERGE; break; }
+        e = launch_round_apply(inst->batch, inst->cfg, s);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "perturbation");
+        delta *= p.alpha;
+        for (int t = 0; t < p.rounding_dual_iters && e == cudaSuccess; ++t) e = launch_iteration(inst->batch, inst->cfg, s);
+        if (e == cudaSuccess) e = launch_addback(inst->batch, inst->cfg, s);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "re-optimisation");
+        ++round;
+    }
+    // objective over the BDD variables on the device; presolve constants on the host
+    double obj_dev = 0.0;
+    std::vector<uint8_t> x(inst->n_vars, 0);
+    if (any) {
+        cudaError_t e = launch_objective(inst->batch, inst->cfg, s);
+        if (e == cudaSuccess)
+            e = copy_async(inst, x.data(), inst->dev.x, inst->n_vars, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail_cuda(inst, e, "objective");
+        InstCtl c;
+        if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
+        obj_dev = c.objective;
+    }
+    for (int32_t i = 0; i < inst->n_vars; ++i) {
+        const int8_t f = inst->dec.fixed[i];
+        if (f == 0 || f == 1) x[i] = static_cast<uint8_t>(f);
+        else if (f == 2) x[i] = inst->cost[i] < 0 ? 1 : 0;
+    }
+    inst->solution = x;
+    inst->objective = obj_dev + inst->dec.const_obj;
+    // exact integer feasibility check of every original row
+    int feasible = 1;
+    for (int32_t j = 0; j < inst->n_rows && feasible; ++j) {
+        int64_t sum = 0;
+        for (int64_t q = inst->row_ptr[j]; q < inst->row_ptr[j + 1]; ++q)
+            sum += static_cast<int64_t>(inst->coef[q]) * x[inst->col[q]];
+        if ((inst->sense[j] <= 0 && sum > inst->rhs[j]) || (inst->sense[j] >= 0 && sum < inst->rhs[j])) feasible = 0;
+    }
+    inst->feasible = feasible;
+    inst->has_solution = true;
+    inst->rounds = round;
+    inst->iterated = false;  // the running bound of the perturbed problem is not an ILP bound
+    inst->pending_T = false;
+    const int32_t en = p.tol > 0 ? 1 : 0;
+    if ((rc = set_ctl_field(inst, offsetof(InstCtl, stop_enabled), &en, sizeof(en))) != FDOG_OK) return rc;
+    if (rounds_used) *rounds_used = round;
+    return status;
+}
+
+int fdog_solution(fdog_instance* inst, uint8_t* x, double* objective, int32_t* feasible) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->has_solution) return FDOG_ESTATE;
+    if (x) std::memcpy(x, inst->solution.data(), inst->solution.size());
+    if (objective) *objective = inst->objective;
+    if (feasible) *feasible = inst->feasible;
+    return FDOG_OK;
+}
+
+int fdog_info(fdog_instance* inst, int64_t* n_vars, int64_t* n_bdds, int64_t* n_slots, int64_t* n_nodes,
+              int64_t* device_bytes) {
+    if (!inst) return FDOG_EINVAL;
+    if (n_vars) *n_vars = inst->n_vars;
+    if (!inst->planned) {
+        if (n_bdds || n_slots || n_nodes || device_bytes) return FDOG_ESTATE;
+        return FDOG_OK;
+    }
+    if (n_bdds) *n_bdds = inst->dec.n_bdds;
+    if (n_slots) *n_slots = inst->dec.n_slots;
+    if (n_nodes) *n_nodes = inst->dec.n_nodes;
+    if (device_bytes)
+        *device_bytes = static_cast<int64_t>(inst->built ? inst->arena_bytes : arena_size(inst)) +
+                        (inst->dev.mm1 ? static_cast<int64_t>(sizeof(float) * inst->dec.slots_pad) : 0);
+    return FDOG_OK;
+}
+
+void fdog_destroy(fdog_instance* inst) {
+    if (!inst) return;
+    if (inst->built || inst->arena || inst->host_ctl) {
+        DeviceGuard g(inst->device);
+        if (inst->stream || inst->arena) cudaStreamSynchronize(inst->stream);
+        if (inst->arena) cudaFree(inst->arena);
+        if (inst->dev.mm1) cudaFree(inst->dev.mm1);
+        if (inst->host_ctl) cudaFreeHost(inst->host_ctl);
+        inst->prof.release();
+        cudaGetLastError();
+    }
+    delete inst;
+}
+
+}  // extern "C"

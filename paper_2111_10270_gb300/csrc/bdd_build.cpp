@@ -1,0 +1,354 @@
+// Host-side decomposition of a 0-1 ILP into one BDD per row (Ex. 1, Def. 4),
+// with presolve, per-signature shape sharing and the tiled device layout.
+//
+// A row's BDD depends only on its coefficient sequence (in ascending variable
+// order), its sense and its right-hand side, so rows with equal signatures
+// share one shape (the MRF encodings have two signatures for millions of
+// rows).  Shapes are built once and instanced per row.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <unordered_map>
+#include <utility>
+
+#include "fdog_internal.h"
+
+namespace fdog {
+
+namespace {
+
+constexpr int64_t kMaxShapeNodes = 1 << 20;
+
+struct PairHash {
+    size_t operator()(const std::pair<int, int>& p) const {
+        return std::hash<int64_t>()((static_cast<int64_t>(p.first) << 32) ^ static_cast<uint32_t>(p.second));
+    }
+};
+
+}  // namespace
+
+// Top-down: the states of layer t are the reachable partial sums of the first
+// t terms that can still be completed into [lo_bound, hi_bound] (interval
+// test on the remaining minimum / maximum).  Bottom-up: a state whose two
+// arcs both fail becomes the BOT terminal, and states of a layer with the same
+// pair of successors are merged, which yields the reduced ordered BDD.
+int build_row_shape(const std::vector<int64_t>& a, bool has_lo, int64_t lo_bound, bool has_hi, int64_t hi_bound,
+                    HostShape& out) {
+    const int k = static_cast<int>(a.size());
+    if (k == 0) return FDOG_EINVAL;
+    std::vector<int64_t> rest_min(k + 1, 0), rest_max(k + 1, 0);
+    for (int t = k - 1; t >= 0; --t) {
+        rest_min[t] = rest_min[t + 1] + std::min<int64_t>(a[t], 0);
+        rest_max[t] = rest_max[t + 1] + std::max<int64_t>(a[t], 0);
+    }
+    auto can_finish = [&](int t, int64_t s) {
+        return (!has_lo || s + rest_max[t] >= lo_bound) && (!has_hi || s + rest_min[t] <= hi_bound);
+    };
+    auto satisfied = [&](int64_t s) { return (!has_lo || s >= lo_bound) && (!has_hi || s <= hi_bound); };
+    if (!can_finish(0, 0)) return FDOG_EINFEASIBLE;
+
+    std::vector<std::vector<int64_t>> states(k);
+    std::vector<std::unordered_map<int64_t, int>> where(k);
+    states[0].push_back(0);
+    where[0][0] = 0;
+    int64_t total = 1;
+    for (int t = 0; t + 1 < k; ++t) {
+        for (int64_t s : states[t]) {
+            for (int b = 0; b < 2; ++b) {
+                int64_t s2 = s + (b ? a[t] : 0);
+                if (!can_finish(t + 1, s2)) continue;
+                if (where[t + 1].emplace(s2, static_cast<int>(states[t + 1].size())).second) {
+                    states[t + 1].push_back(s2);
+                    if (++total > kMaxShapeNodes) return FDOG_ENOMEM;
+                }
+            }
+        }
+    }
+
+    // canon[t][q]: node id within layer t of state q, or kArcBot
+    std::vector<std::vector<int>> canon(k);
+    std::vector<std::vector<std::pair<int, int>>> layer_nodes(k);  // (lo, hi) per canonical node
+    for (int t = k - 1; t >= 0; --t) {
+        std::unordered_map<std::pair<int, int>, int, PairHash> seen;
+        canon[t].assign(states[t].size(), kArcBot);
+        for (size_t q = 0; q < states[t].size(); ++q) {
+            int arcs[2];
+            for (int b = 0; b < 2; ++b) {
+                int64_t s2 = states[t][q] + (b ? a[t] : 0);
+                if (t + 1 == k) {
+                    arcs[b] = satisfied(s2) ? kArcTop : kArcBot;
+                } else if (!can_finish(t + 1, s2)) {
+                    arcs[b] = kArcBot;
+                } else {
+                    arcs[b] = canon[t + 1][where[t + 1].at(s2)];
+                }
+            }
+            if (arcs[0] == kArcBot && arcs[1] == kArcBot) continue;
+            auto key = std::make_pair(arcs[0], arcs[1]);
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                it = seen.emplace(key, static_cast<int>(layer_nodes[t].size())).first;
+                layer_nodes[t].push_back(key);
+            }
+            canon[t][q] = it->second;
+        }
+    }
+    if (canon[0][0] == kArcBot) return FDOG_EINFEASIBLE;
+
+    out = HostShape();
+    out.k = k;
+    out.lstart.resize(k + 1);
+    int base = 0;
+    for (int t = 0; t < k; ++t) {
+        out.lstart[t] = base;
+        base += static_cast<int>(layer_nodes[t].size());
+        out.width = std::max<int>(out.width, static_cast<int>(layer_nodes[t].size()));
+    }
+    out.lstart[k] = base;
+    out.lo.resize(base);
+    out.hi.resize(base);
+    for (int t = 0; t < k; ++t) {
+        int next = (t + 1 < k) ? out.lstart[t + 1] : 0;
+        for (size_t v = 0; v < layer_nodes[t].size(); ++v) {
+            auto [l, h] = layer_nodes[t][v];
+            out.lo[out.lstart[t] + v] = l >= 0 ? next + l : l;
+            out.hi[out.lstart[t] + v] = h >= 0 ? next + h : h;
+        }
+    }
+    return FDOG_OK;
+}
+
+namespace {
+
+struct Analysis {
+    int status = FDOG_OK;
+    bool full_cube = false;
+    std::vector<int8_t> forced;  // per layer: -1 free, 0 / 1 forced value
+    HostShape shape;
+};
+
+Analysis analyse(const std::vector<int64_t>& a, int8_t sense, int64_t rhs) {
+    Analysis an;
+    an.status = build_row_shape(a, sense >= 0, rhs, sense <= 0, rhs, an.shape);
+    if (an.status != FDOG_OK) return an;
+    const HostShape& s = an.shape;
+    an.full_cube = true;
+    an.forced.assign(s.k, -1);
+    for (int t = 0; t < s.k; ++t) {
+        int b = s.lstart[t], e = s.lstart[t + 1];
+        if (e - b != 1 || s.lo[b] != s.hi[b] || s.lo[b] == kArcBot) an.full_cube = false;
+        bool no_one = true, no_zero = true;
+        for (int v = b; v < e; ++v) {
+            if (s.hi[v] != kArcBot) no_one = false;
+            if (s.lo[v] != kArcBot) no_zero = false;
+        }
+        // every node lies on a root-TOP path, so a layer without 1-arcs forces 0
+        if (no_one) an.forced[t] = 0;
+        else if (no_zero) an.forced[t] = 1;
+    }
+    return an;
+}
+
+std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) {
+    std::string key(1 + 8 + 8 * a.size(), '\0');
+    key[0] = static_cast<char>(sense);
+    std::memcpy(&key[1], &rhs, 8);
+    std::memcpy(&key[9], a.data(), 8 * a.size());
+    return key;
+}
+
+}  // namespace
+
+int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
+                        const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
+                        Decomposition& out, std::string& err) {
+    out = Decomposition();
+    out.fixed.assign(n_vars, -1);
+
+    // rows with non-zero entries sorted by variable (Alg. 1 visits I_j ascending)
+    std::vector<int64_t> rb(n_rows + 1, 0);
+    std::vector<int32_t> rv;
+    std::vector<int64_t> ra;
+    rv.reserve(row_ptr[n_rows]);
+    ra.reserve(row_ptr[n_rows]);
+    {
+        std::vector<std::pair<int32_t, int32_t>> tmp;
+        for (int32_t j = 0; j < n_rows; ++j) {
+            tmp.clear();
+            for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q)
+                if (coef[q] != 0) tmp.emplace_back(col[q], coef[q]);
+            if (!std::is_sorted(tmp.begin(), tmp.end())) std::sort(tmp.begin(), tmp.end());
+            for (auto& [c, v] : tmp) { rv.push_back(c); ra.push_back(v); }
+            rb[j + 1] = static_cast<int64_t>(rv.size());
+        }
+    }
+
+    std::unordered_map<std::string, int> cache;
+    std::vector<Analysis> analyses;
+    std::vector<int> row_an(n_rows, -1);
+    std::vector<uint8_t> alive(n_rows, 1);
+    std::vector<int64_t> a;
+    auto residual = [&](int32_t j, std::vector<int64_t>& coefs, int64_t& b) {
+        coefs.clear();
+        b = rhs[j];
+        for (int64_t q = rb[j]; q < rb[j + 1]; ++q) {
+            int8_t f = out.fixed[rv[q]];
+            if (f == 0 || f == 1) b -= ra[q] * f;
+            else coefs.push_back(ra[q]);
+        }
+    };
+
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int32_t j = 0; j < n_rows; ++j) {
+            if (!alive[j]) continue;
+            int64_t b;
+            residual(j, a, b);
+            if (a.empty()) {
+                bool ok = (sense[j] > 0 || 0 <= b) && (sense[j] < 0 || 0 >= b);
+                if (!ok) { err = "row " + std::to_string(j) + " violated by fixed variables"; return FDOG_EINFEASIBLE; }
+                alive[j] = 0;
+                continue;
+            }
+            std::string key = signature(sense[j], b, a);
+            auto it = cache.find(key);
+            int id;
+            if (it == cache.end()) {
+                id = static_cast<int>(analyses.size());
+                analyses.push_back(analyse(a, sense[j], b));
+                cache.emplace(std::move(key), id);
+            } else {
+                id = it->second;
+            }
+            const Analysis& an = analyses[id];
+            if (an.status == FDOG_EINFEASIBLE) { err = "row " + std::to_string(j) + " is infeasible"; return FDOG_EINFEASIBLE; }
+            if (an.status != FDOG_OK) { err = "row " + std::to_string(j) + ": BDD too large"; return an.status; }
+            row_an[j] = id;
+            if (an.full_cube) { alive[j] = 0; continue; }
+            int t = 0;
+            for (int64_t q = rb[j]; q < rb[j + 1]; ++q) {
+                int8_t f = out.fixed[rv[q]];
+                if (f == 0 || f == 1) continue;
+                if (an.forced[t] >= 0) { out.fixed[rv[q]] = an.forced[t]; changed = true; }
+                ++t;
+            }
+        }
+    }
+
+    // surviving rows: their analysis holds the final shape
+    std::vector<int> shape_of_an(analyses.size(), -1);
+    struct Bdd { int cls; int shape; int32_t row; };
+    std::vector<Bdd> bdds;
+    for (int32_t j = 0; j < n_rows; ++j) {
+        if (!alive[j]) continue;
+        int id = row_an[j];
+        if (shape_of_an[id] < 0) {
+            const HostShape& s = analyses[id].shape;
+            int cls = class_of(s.width, s.k);
+            if (cls < 0 || (!class_is_reg(cls) && s.k > kMaxLayersSmem)) {
+                err = "row " + std::to_string(j) + ": BDD width " + std::to_string(s.width) + " / length " +
+                      std::to_string(s.k) + " exceeds the sweep kernels' limits";
+                return FDOG_EUNSUPPORTED;
+            }
+            shape_of_an[id] = static_cast<int>(out.shapes.size());
+            out.shapes.push_back(s);
+            out.shape_cls.push_back(cls);
+        }
+        int sh = shape_of_an[id];
+        bdds.push_back({out.shape_cls[sh], sh, j});
+    }
+    std::stable_sort(bdds.begin(), bdds.end(), [](const Bdd& x, const Bdd& y) {
+        return x.cls != y.cls ? x.cls < y.cls : x.shape < y.shape;
+    });
+
+    // presolve constants
+    std::vector<int32_t> cnt(n_vars, 0);
+    for (const Bdd& d : bdds)
+        for (int64_t q = rb[d.row]; q < rb[d.row + 1]; ++q)
+            if (out.fixed[rv[q]] == -1) cnt[rv[q]]++;
+    for (int32_t i = 0; i < n_vars; ++i) {
+        if (out.fixed[i] == 0 || out.fixed[i] == 1) {
+            out.const_lb += cost[i] * out.fixed[i];
+        } else if (cnt[i] == 0) {
+            out.fixed[i] = 2;
+            out.const_lb += std::min(cost[i], 0.0);
+        }
+    }
+    out.const_obj = out.const_lb;
+
+    // templates
+    out.shape_dev.resize(out.shapes.size());
+    for (size_t s = 0; s < out.shapes.size(); ++s) {
+        const HostShape& h = out.shapes[s];
+        int W = class_width(out.shape_cls[s]);
+        while (out.tpl.size() % 8) out.tpl.push_back(0);  // 16-byte aligned vector loads
+        ShapeDev d{h.k, static_cast<int32_t>(out.tpl.size()), W, 0};
+        out.shape_dev[s] = d;
+        for (int t = 0; t < h.k; ++t) {
+            int b = h.lstart[t], e = h.lstart[t + 1];
+            int nb = (t + 1 < h.k) ? h.lstart[t + 1] : 0;
+            for (int v = 0; v < W; ++v) {
+                uint8_t lo = kCodeBot, hi = kCodeBot;
+                if (b + v < e) {
+                    int l = h.lo[b + v], u = h.hi[b + v];
+                    lo = l == kArcTop ? kCodeTop : (l == kArcBot ? kCodeBot : static_cast<uint8_t>(l - nb));
+                    hi = u == kArcTop ? kCodeTop : (u == kArcBot ? kCodeBot : static_cast<uint8_t>(u - nb));
+                }
+                out.tpl.push_back(static_cast<uint16_t>(lo | (hi << 8)));
+            }
+        }
+    }
+
+    // tiles: runs of equal shape, kTile BDDs each, grouped by kernel class
+    out.cls_tile_begin.assign(kNumClasses + 1, 0);
+    int64_t slot = 0;
+    for (size_t q = 0; q < bdds.size();) {
+        size_t e = q;
+        while (e < bdds.size() && e - q < static_cast<size_t>(kTile) && bdds[e].shape == bdds[q].shape) ++e;
+        TileDev t{bdds[q].shape, static_cast<int32_t>(slot), static_cast<int32_t>(e - q), static_cast<int32_t>(q)};
+        int k = out.shapes[bdds[q].shape].k;
+        slot += static_cast<int64_t>(k) * kTile;
+        if (slot > INT32_MAX) { err = "more than 2^31 padded slots"; return FDOG_EUNSUPPORTED; }
+        out.tiles.push_back(t);
+        out.cls_tile_begin[bdds[q].cls + 1]++;
+        int cls = bdds[q].cls;
+        out.kmax[cls] = std::max(out.kmax[cls], k);
+        q = e;
+    }
+    for (int c = 0; c < kNumClasses; ++c) out.cls_tile_begin[c + 1] += out.cls_tile_begin[c];
+    out.slots_pad = slot;
+    out.var.assign(slot, -1);
+    out.bdd_row.resize(bdds.size());
+    out.bdd_shape.resize(bdds.size());
+    out.bdd_slot0.resize(bdds.size());
+    out.row_bdd.assign(n_rows, -1);
+    out.n_bdds = static_cast<int64_t>(bdds.size());
+    for (const TileDev& t : out.tiles) {
+        for (int l = 0; l < t.n_valid; ++l) {
+            const Bdd& d = bdds[t.bdd_base + l];
+            out.bdd_row[t.bdd_base + l] = d.row;
+            out.bdd_shape[t.bdd_base + l] = d.shape;
+            out.bdd_slot0[t.bdd_base + l] = t.slot_base + l;
+            out.row_bdd[d.row] = t.bdd_base + l;
+            out.n_nodes += out.shapes[d.shape].lstart.back();
+            int layer = 0;
+            for (int64_t q = rb[d.row]; q < rb[d.row + 1]; ++q) {
+                if (out.fixed[rv[q]] != -1) continue;
+                out.var[t.slot_base + static_cast<int64_t>(layer) * kTile + l] = rv[q];
+                ++layer;
+            }
+        }
+    }
+    // per-variable slot lists (ascending padded position: a fixed summation order)
+    out.csr_off.assign(n_vars + 1, 0);
+    for (int32_t i = 0; i < n_vars; ++i) out.csr_off[i + 1] = out.csr_off[i] + cnt[i];
+    out.n_slots = out.csr_off[n_vars];
+    out.csr_pos.resize(out.n_slots);
+    std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
+    for (int64_t p = 0; p < slot; ++p)
+        if (out.var[p] >= 0) out.csr_pos[fill[out.var[p]]++] = static_cast<int32_t>(p);
+    return FDOG_OK;
+}
+
+}  // namespace fdog

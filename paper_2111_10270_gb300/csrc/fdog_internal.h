@@ -1,0 +1,153 @@
+// Internal types shared by the host-side builder and the CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fastdog.h"
+
+namespace fdog {
+
+// One warp processes one tile of kTile BDDs of the same shape; lane l owns
+// BDD l of the tile (thread per BDD).  Slots of a tile are interleaved:
+// slot (layer t, lane l) lives at slot_base + t * kTile + l, so every
+// per-layer load and store of a warp is one coalesced 128-byte transaction.
+constexpr int kTile = 32;
+
+// Node-successor codes of the shape templates (one uint8 per arc).
+constexpr uint8_t kCodeTop = 0xFE;
+constexpr uint8_t kCodeBot = 0xFF;
+
+// Kernel classes: maximum layer width W of the shape (register arrays of W
+// shortest-path labels per layer) and whether all per-layer state fits in
+// registers (W <= kRegW and k <= kRegK) or lives in shared memory.
+constexpr int kRegK = 8;
+constexpr int kRegW = 4;
+constexpr int kWidths[4] = {2, 4, 8, 16};
+constexpr int kNumWidths = 4;
+constexpr int kMaxWidth = 16;
+constexpr int kMaxLayersSmem = 256;  // longest row the shared-memory kernels take
+constexpr int kNumClasses = 2 * kNumWidths;  // (width index) x (register | smem)
+
+inline int class_of(int width, int k) {
+    int wi = 0;
+    while (wi < kNumWidths && kWidths[wi] < width) ++wi;
+    if (wi == kNumWidths) return -1;
+    return wi * 2 + ((k <= kRegK && kWidths[wi] <= kRegW) ? 0 : 1);
+}
+inline int class_width(int cls) { return kWidths[cls / 2]; }
+inline bool class_is_reg(int cls) { return (cls % 2) == 0; }
+
+struct ShapeDev {
+    int32_t k;        // layers (= variables of the row)
+    int32_t tpl_off;  // offset (in uint16 units) of the template: k * W entries
+    int32_t width;    // W of its class
+    int32_t pad;
+};
+
+struct TileDev {
+    int32_t shape;
+    int32_t slot_base;
+    int32_t n_valid;   // BDDs in this tile (1..kTile)
+    int32_t bdd_base;  // index of lane 0's BDD in the instance's BDD order
+};
+
+constexpr int kLbRing = 64;
+
+// Device-resident control block of one instance.
+struct InstCtl {
+    double lb_ring[kLbRing];  // running lower bound after iteration t at [t % kLbRing]
+    double lb_last;           // running lower bound after the last iteration
+    double lb_eval;           // result of the last evaluation reduction
+    double objective;         // c^T x of the last rounding (without presolve constants)
+    int32_t iter;             // dual iterations completed since the build
+    int32_t done;             // stopping rule met: update kernels become no-ops
+    int32_t ticket;           // last-block ticket of the lower-bound reduction
+    int32_t obj_ticket;
+    int32_t n_disagree;       // rounding: variables whose M_ij do not share one strict sign
+    int32_t error;
+    int32_t stop_enabled;
+    int32_t window;
+    int32_t min_iters;
+    int32_t since_reset;      // iterations since the stopping history was reset
+    double tol;
+};
+
+// Everything a kernel needs to know about one instance (device pointers).
+struct InstDev {
+    const TileDev* tiles;
+    const ShapeDev* shapes;
+    const uint16_t* tpl;     // per shape: k * W codes (lo | hi << 8)
+    float* lam;              // [slots_pad] multipliers lambda^j_i
+    const int32_t* var;      // [slots_pad] variable of each slot, -1 for padding
+    float* mm0;              // [slots_pad] min-marginal outputs (m0, or M)
+    float* mm1;              // [slots_pad] min-marginal output m1
+    float* T;                // [n] deferred term  omega/|J_i| sum_k Mbar_ik
+    float* C;                // [n] target sum_j lambda^j_i (= c_i, perturbed by rounding)
+    const int32_t* csr_off;  // [n + 1]
+    const int32_t* csr_pos;  // [slots] padded slot positions of each variable, ascending
+    const double* cost;      // [n]
+    float* pert;             // [n] rounding perturbation of this round
+    uint8_t* x;              // [n] rounded solution
+    double* tile_lb;         // [n_tiles] per-tile partial of the lower bound
+    double* chunk_lb;        // [n_chunks] per-chunk partials of the lower-bound reduction
+    double* obj_chunk;       // [n_obj_chunks]
+    InstCtl* ctl;
+    int32_t n_tiles;
+    int32_t n_vars;
+    int32_t n_chunks;
+    int32_t n_obj_chunks;
+    float omega;
+    float pad0;
+    double const_lb;
+};
+
+// ---------------------------------------------------------------------------
+// host-side decomposition
+// ---------------------------------------------------------------------------
+constexpr int kArcTop = -1;
+constexpr int kArcBot = -2;
+
+struct HostShape {
+    int k = 0;
+    int width = 0;                 // maximum nodes in a layer
+    std::vector<int> lstart;       // k + 1
+    std::vector<int> lo, hi;       // per node: node index, kArcTop or kArcBot
+};
+
+struct Decomposition {
+    // presolve
+    std::vector<int8_t> fixed;     // -1 in a BDD, 0/1 fixed, 2 in no row
+    double const_lb = 0.0;         // sum fixed c x + sum free min(c, 0)
+    double const_obj = 0.0;        // sum fixed c x + sum free c [c < 0]
+    // BDDs in layout order
+    std::vector<HostShape> shapes;
+    std::vector<int> shape_cls;    // kernel class of each shape
+    std::vector<int32_t> bdd_row;  // original row of each BDD (layout order)
+    std::vector<int32_t> bdd_shape;  // shape of each BDD
+    std::vector<int32_t> bdd_slot0;  // padded slot of layer 0 of each BDD (layer t at + t * kTile)
+    std::vector<int32_t> row_bdd;    // BDD of each original row, -1 if presolve removed it
+    std::vector<TileDev> tiles;
+    std::vector<int32_t> cls_tile_begin;  // kNumClasses + 1 (tiles sorted by class)
+    std::vector<int32_t> var;      // padded slots
+    std::vector<int32_t> csr_off, csr_pos;
+    std::vector<ShapeDev> shape_dev;
+    std::vector<uint16_t> tpl;
+    int64_t n_bdds = 0, n_slots = 0, n_nodes = 0, slots_pad = 0;
+    int kmax[kNumClasses] = {0};
+};
+
+// Builds the decomposition: presolve, BDDs per row (shared per row
+// signature), tiles, interleaved slots and the per-variable slot lists.
+// Returns an FDOG_* status.
+int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
+                        const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
+                        Decomposition& out, std::string& err);
+
+// BDD of { x in {0,1}^k : lo_bound <= sum a_t x_t <= hi_bound } (either bound optional).
+int build_row_shape(const std::vector<int64_t>& a, bool has_lo, int64_t lo_bound, bool has_hi, int64_t hi_bound,
+                    HostShape& out);
+
+}  // namespace fdog

@@ -1,0 +1,92 @@
+// The library-owned instance behind the opaque fdog_instance handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "fdog_internal.h"
+#include "kernels.h"
+
+namespace fdog {
+
+// prefix ints of a one-instance batch: per class 3 (prefix[2], first[1]) + 4 x 2
+constexpr int kPrefixInts = 3 * kNumClasses + 8;
+
+struct DevArrays {
+    InstDev* inst = nullptr;
+    InstCtl* ctl = nullptr;
+    TileDev* tiles = nullptr;
+    ShapeDev* shapes = nullptr;
+    uint16_t* tpl = nullptr;
+    float* lam = nullptr;
+    int32_t* var = nullptr;
+    float* mm0 = nullptr;
+    float* mm1 = nullptr;  // separate allocation, made on first use
+    float* T = nullptr;
+    float* C = nullptr;
+    float* pert = nullptr;
+    uint8_t* x = nullptr;
+    double* cost = nullptr;
+    int32_t* csr_off = nullptr;
+    int32_t* csr_pos = nullptr;
+    double* tile_lb = nullptr;
+    double* chunk_lb = nullptr;
+    double* obj_chunk = nullptr;
+    int32_t* prefix = nullptr;
+};
+
+}  // namespace fdog
+
+struct fdog_instance {
+    // the ILP as given (copied at create)
+    int32_t n_vars = 0;
+    int32_t n_rows = 0;
+    std::vector<double> cost;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col, coef;
+    std::vector<int8_t> sense;
+    std::vector<int64_t> rhs;
+    fdog_params params{};
+
+    // decomposition and device state
+    bool planned = false;
+    bool built = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    fdog::Decomposition dec;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    fdog::DevArrays dev;
+    fdog::InstDev hdesc{};
+    fdog::DevBatch batch;
+    fdog::LaunchCfg cfg;
+    fdog::InstCtl* host_ctl = nullptr;  // pinned
+    fdog::Profiler prof;
+
+    // host-side view of the dual state
+    bool pending_T = false;  // deferred differences of the last pass not yet added back
+    bool iterated = false;   // iterations ran since the last add-back (running bound available)
+
+    // rounding result
+    bool has_solution = false;
+    std::vector<uint8_t> solution;
+    double objective = 0.0;
+    int32_t feasible = 0;
+    int32_t rounds = 0;
+
+    int64_t h2d_bytes = 0;  // host-to-device bytes copied by the library for this instance
+    int64_t d2h_bytes = 0;
+
+    std::string last_error;
+};
+
+namespace fdog {
+int plan(fdog_instance* inst);
+size_t arena_size(const fdog_instance* inst);
+int fail_cuda(fdog_instance* inst, cudaError_t e, const char* where);
+cudaError_t copy_async(fdog_instance* inst, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);
+int read_ctl(fdog_instance* inst, InstCtl& out);
+int addback(fdog_instance* inst);
+}  // namespace fdog

@@ -1,0 +1,435 @@
+// sm_103a kernels of the FastDOG dual hot path.
+//
+// Work decomposition
+//   * sweep kernels: one warp per tile of 32 BDDs of one shape, one thread per
+//     BDD.  All per-layer loads/stores of a warp are single 128-byte
+//     transactions (interleaved slots).  The shape template (successor codes
+//     per layer and node) is read with warp-uniform loads.  Shortest-path
+//     labels of the direction opposite to the pass are recomputed on chip at
+//     the start of each pass, so no per-node state ever goes to HBM; per-slot
+//     multipliers are the only state the sweeps stream.
+//   * deferred sums: one thread per variable sums its slots in a fixed order
+//     (deterministic; no floating-point atomics).
+//   * lower bound: FP32 per BDD, compensated FP32 within a warp, FP64
+//     Neumaier across tiles with a fixed chunking per instance, so the bound
+//     of an instance does not depend on what else is in the batch.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+#include "sweep.cuh"
+
+namespace fdog {
+namespace {
+
+using dev::find_inst;
+
+struct FlatArgs {
+    const InstDev* insts;
+    const int32_t* prefix;
+    int32_t n_inst;
+    int32_t total;
+};
+
+// T_i = (C_i - sum_j lambda^j_i) / |J_i|.  Right after a pass, Prop. 1 gives
+// sum_j lambda^j_i + omega sum_j M_ij = C_i, so T_i equals the averaged
+// deferred term omega / |J_i| sum_k Mbar_ik of Eq. 5.
+__global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        if (I->ctl->done) continue;
+        const int i = g - __ldg(a.prefix + ii);
+        const int b = I->csr_off[i], e = I->csr_off[i + 1];
+        if (b == e) continue;
+        const float* __restrict__ lam = I->lam;
+        const int32_t* __restrict__ pos = I->csr_pos;
+        float s = 0.f;
+        for (int p = b; p < e; ++p) s += lam[pos[p]];
+        I->T[i] = (I->C[i] - s) / static_cast<float>(e - b);
+    }
+}
+
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+}
+
+struct LbArgs {
+    const InstDev* insts;
+    const int32_t* prefix;
+    int32_t n_inst;
+    int32_t target;
+};
+
+__global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
+    __shared__ double ss[256], sc[256];
+    const int g = blockIdx.x;
+    const int ii = find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    InstCtl* ctl = I->ctl;
+    if (a.target == kLbIterate && ctl->done) return;
+    const int c = g - __ldg(a.prefix + ii);
+    const int t0 = c * kLbChunk;
+    const int t1 = min(t0 + kLbChunk, I->n_tiles);
+    double s = 0.0, cp = 0.0;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) neumaier(s, cp, I->tile_lb[t]);
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = cp;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double x = ss[threadIdx.x], y = ss[threadIdx.x + w], cc = sc[threadIdx.x] + sc[threadIdx.x + w];
+            neumaier(x, cc, y);
+            ss[threadIdx.x] = x;
+            sc[threadIdx.x] = cc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        I->chunk_lb[c] = ss[0] + sc[0];
+        __threadfence();
+        const int ticket = atomicAdd(&ctl->ticket, 1);
+        if (ticket == I->n_chunks - 1) {
+            __threadfence();
+            double S = 0.0, Cc = 0.0;
+            for (int q = 0; q < I->n_chunks; ++q) neumaier(S, Cc, __ldcg(I->chunk_lb + q));
+            neumaier(S, Cc, I->const_lb);
+            const double lb = S + Cc;
+            ctl->ticket = 0;
+            if (a.target == kLbIterate) {
+                const int it = ctl->iter;
+                ctl->lb_ring[it % kLbRing] = lb;
+                ctl->lb_last = lb;
+                ctl->iter = it + 1;
+                const int since = ++ctl->since_reset;
+                if (ctl->stop_enabled && since >= ctl->min_iters && since > ctl->window) {
+                    const double prev = ctl->lb_ring[(it - ctl->window) % kLbRing];
+                    if (lb - prev <= ctl->tol * fmax(fabs(lb), 1.0)) ctl->done = 1;
+                }
+            } else {
+                ctl->lb_eval = lb;
+            }
+        }
+    }
+}
+
+// C_i = c_i, T_i = 0 (M-bar = 0)
+__global__ void __launch_bounds__(256) init_vars_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        const int i = g - __ldg(a.prefix + ii);
+        I->C[i] = static_cast<float>(I->cost[i]);
+        I->T[i] = 0.f;
+    }
+}
+
+// lambda^j_i = c_i / |J_i| (Alg. 1 initialisation); padding slots get 0
+__global__ void __launch_bounds__(256) init_lam_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        const int p = g - __ldg(a.prefix + ii);
+        const int v = I->var[p];
+        float l = 0.f;
+        if (v >= 0) l = I->C[v] / static_cast<float>(I->csr_off[v + 1] - I->csr_off[v]);
+        I->lam[p] = l;
+    }
+}
+
+// final loop of Alg. 1: lambda^j_i += T_i
+__global__ void __launch_bounds__(256) addback_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        const int p = g - __ldg(a.prefix + ii);
+        const int v = I->var[p];
+        if (v >= 0) I->lam[p] += I->T[v];
+    }
+}
+
+__global__ void __launch_bounds__(256) zero_T_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        I->T[g - __ldg(a.prefix + ii)] = 0.f;
+    }
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014) of one counter value
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct RoundArgs {
+    FlatArgs f;
+    int32_t round;
+    double delta;
+    uint64_t seed;
+};
+
+// Alg. 2 per variable: agreement test on M_ij and the perturbation of this round
+__global__ void __launch_bounds__(256) round_test_kernel(RoundArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.f.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.f.prefix, a.f.n_inst, g);
+        const InstDev* __restrict__ I = a.f.insts + ii;
+        const int i = g - __ldg(a.f.prefix + ii);
+        const int b = I->csr_off[i], e = I->csr_off[i + 1];
+        if (b == e) continue;
+        int npos = 0, nneg = 0, nzero = 0;
+        float sum = 0.f;
+        for (int p = b; p < e; ++p) {
+            const float m = I->mm0[I->csr_pos[p]];
+            npos += m > 0.f;
+            nneg += m < 0.f;
+            nzero += m == 0.f;
+            sum += m;
+        }
+        const int cnt = e - b;
+        if (!(npos == cnt || nneg == cnt)) atomicAdd(&I->ctl->n_disagree, 1);
+        I->x[i] = sum < 0.f ? 1 : 0;
+        const uint64_t h = mix64(a.seed ^ (static_cast<uint64_t>(static_cast<uint32_t>(a.round)) << 32) ^
+                                 static_cast<uint64_t>(static_cast<uint32_t>(i)));
+        const double r = 2.0 * (static_cast<double>(h >> 11) * 0x1.0p-53) - 1.0;
+        double p;
+        if (npos == cnt) p = a.delta;
+        else if (nneg == cnt) p = -a.delta;
+        else if (nzero == cnt) p = r * a.delta;
+        else {
+            const double sg = sum > 0.f ? 1.0 : (sum < 0.f ? -1.0 : (r >= 0.0 ? 1.0 : -1.0));
+            p = sg * fabs(r) * a.delta;
+        }
+        I->pert[i] = static_cast<float>(p);
+    }
+}
+
+// Alg. 2: lambda^j_i += p_i for all j in J_i (only if some variable disagrees)
+__global__ void __launch_bounds__(256) round_apply_kernel(FlatArgs a) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        if (I->ctl->n_disagree == 0) continue;
+        const int i = g - __ldg(a.prefix + ii);
+        const int b = I->csr_off[i], e = I->csr_off[i + 1];
+        if (b == e) continue;
+        const float p = I->pert[i];
+        for (int q = b; q < e; ++q) I->lam[I->csr_pos[q]] += p;
+        I->C[i] += p * static_cast<float>(e - b);
+        I->T[i] = 0.f;
+    }
+}
+
+// c^T x over the variables inside BDDs, FP64 Neumaier with fixed chunking
+__global__ void __launch_bounds__(256) objective_kernel(LbArgs a) {
+    __shared__ double ss[256], sc[256];
+    const int g = blockIdx.x;
+    const int ii = find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    InstCtl* ctl = I->ctl;
+    const int c = g - __ldg(a.prefix + ii);
+    const int v0 = c * kObjChunk, v1 = min(v0 + kObjChunk, I->n_vars);
+    double s = 0.0, cp = 0.0;
+    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x)
+        if (I->csr_off[i + 1] > I->csr_off[i] && I->x[i]) neumaier(s, cp, I->cost[i]);
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = cp;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double x = ss[threadIdx.x], y = ss[threadIdx.x + w], cc = sc[threadIdx.x] + sc[threadIdx.x + w];
+            neumaier(x, cc, y);
+            ss[threadIdx.x] = x;
+            sc[threadIdx.x] = cc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        I->obj_chunk[c] = ss[0] + sc[0];
+        __threadfence();
+        const int ticket = atomicAdd(&ctl->obj_ticket, 1);
+        if (ticket == I->n_obj_chunks - 1) {
+            __threadfence();
+            double S = 0.0, Cc = 0.0;
+            for (int q = 0; q < I->n_obj_chunks; ++q) neumaier(S, Cc, __ldcg(I->obj_chunk + q));
+            ctl->objective = S + Cc;
+            ctl->obj_ticket = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+inline int blocks_for(int total, int per_block, int cap) {
+    int b = (total + per_block - 1) / per_block;
+    return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+}  // namespace
+
+int smem_max_layers(int width) {
+    // per warp: kTile columns x (lambda, T, W labels) floats per layer; at least one warp per block
+    return (200 * 1024) / (kTile * 4 * (2 + width));
+}
+
+cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
+    for (int cls = 0; cls < kNumClasses; ++cls) {
+        const int total = b.tiles_total[cls];
+        if (total == 0) continue;
+        const bool reg = class_is_reg(cls);
+        const int W = class_width(cls);
+        int wpb = cfg.warps_per_block;
+        size_t smem = 0;
+        int kstride = 0;
+        if (!reg) {
+            kstride = b.kmax[cls];
+            const size_t per_warp = static_cast<size_t>(kstride) * kTile * (2 + W) * sizeof(float);
+            while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
+            smem = per_warp * wpb;
+        }
+        SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags};
+        const int blocks = blocks_for(total, wpb, cfg.num_sms * (2048 / (32 * wpb)));
+        const bool timed = cfg.prof && cfg.prof->on && (mode == kFwdUpdate || mode == kBwdUpdate);
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+        cudaError_t e;
+        switch (W) {
+            case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+            case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+            case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+            default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+        }
+        if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(true, ev0, ev1); }
+        cfg.count();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static FlatArgs flat(const DevBatch& b, const int32_t* prefix, int total) {
+    return FlatArgs{b.insts, prefix, b.n_inst, total};
+}
+
+cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.vars_total == 0) return cudaSuccess;
+    const bool timed = cfg.prof && cfg.prof->on;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+    reduce_T_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+        flat(b, b.var_prefix, b.vars_total));
+    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
+    cfg.count();
+    return cudaGetLastError();
+}
+
+cudaEvent_t Profiler::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Profiler::drain(int64_t& n_sweep, double& ms_sweep, int64_t& n_reduce, double& ms_reduce) {
+    auto sum = [&](std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, int64_t& n, double& ms) {
+        for (auto& [a, b] : v) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, a, b) == cudaSuccess) { ms += t; ++n; }
+            pool.push_back(a);
+            pool.push_back(b);
+        }
+        v.clear();
+    };
+    sum(sweep, n_sweep, ms_sweep);
+    sum(reduce, n_reduce, ms_reduce);
+    cudaGetLastError();
+}
+
+void Profiler::release() {
+    for (auto& [a, b] : sweep) { pool.push_back(a); pool.push_back(b); }
+    for (auto& [a, b] : reduce) { pool.push_back(a); pool.push_back(b); }
+    sweep.clear();
+    reduce.clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+
+cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.chunks_total == 0) return cudaSuccess;
+    cfg.count();
+    lb_reduce_kernel<<<b.chunks_total, 256, 0, s>>>(LbArgs{b.insts, b.chunk_prefix, b.n_inst, target});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    cfg.count((b.vars_total > 0) + (b.slots_total > 0));
+    if (b.vars_total > 0)
+        init_vars_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+            flat(b, b.var_prefix, b.vars_total));
+    if (b.slots_total > 0)
+        init_lam_kernel<<<blocks_for(b.slots_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+            flat(b, b.slot_prefix, b.slots_total));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_addback(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    cfg.count(b.slots_total > 0);
+    if (b.slots_total > 0)
+        addback_kernel<<<blocks_for(b.slots_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+            flat(b, b.slot_prefix, b.slots_total));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_zero_T(b, cfg, s);
+}
+
+cudaError_t launch_zero_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    cfg.count(b.vars_total > 0);
+    if (b.vars_total > 0)
+        zero_T_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+            flat(b, b.var_prefix, b.vars_total));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_test(const DevBatch& b, int round, double delta, uint64_t seed, const LaunchCfg& cfg,
+                              cudaStream_t s) {
+    if (b.vars_total == 0) return cudaSuccess;
+    cfg.count();
+    round_test_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+        RoundArgs{flat(b, b.var_prefix, b.vars_total), round, delta, seed});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_apply(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.vars_total == 0) return cudaSuccess;
+    cfg.count();
+    round_apply_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+        flat(b, b.var_prefix, b.vars_total));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.objchunks_total == 0) return cudaSuccess;
+    cfg.count();
+    objective_kernel<<<b.objchunks_total, 256, 0, s>>>(LbArgs{b.insts, b.objchunk_prefix, b.n_inst, 0});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_sweep(b, kFwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
+    if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
+    if ((e = launch_sweep(b, kBwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
+    if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
+    return launch_lb_reduce(b, kLbIterate, cfg, s);
+}
+
+}  // namespace fdog

@@ -1,0 +1,101 @@
+// Launchers of the sm_103a kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "fdog_internal.h"
+
+namespace fdog {
+
+enum SweepMode : int {
+    kFwdUpdate = 0,  // ascending pass of Alg. 1 (Alg. 3 shortest paths, Eq. 5 updates)
+    kBwdUpdate = 1,  // descending pass of Alg. 1 (Alg. 4 shortest paths, Eq. 5 updates)
+    kMinMarg = 2,    // min-marginals of every slot (Eq. 6), no update
+    kEval = 3,       // energies E^j only, no update
+};
+
+// kMinMarg / kEval flags
+constexpr int kMMAddT = 1;   // evaluate at lambda + T (the add-back of Alg. 1)
+constexpr int kMMBoth = 2;   // write m0 and m1 (else M = m1 - m0 into mm0)
+
+// lower-bound reduction targets
+constexpr int kLbIterate = 0;  // running bound of an iteration: ring, counter, stopping rule
+constexpr int kLbEval = 1;     // evaluation: InstCtl::lb_eval
+
+constexpr int kLbChunk = 4096;   // tiles per block of the lower-bound reduction
+constexpr int kObjChunk = 8192;  // variables per block of the objective reduction
+
+// Device-side description of a batch of instances (one or many).  Work of
+// every kernel is a flat index space over all instances; prefix arrays map a
+// flat index back to (instance, local index).
+struct DevBatch {
+    InstDev* insts = nullptr;
+    int32_t* tile_prefix[kNumClasses] = {};  // [n_inst + 1] tiles of class c per instance
+    int32_t* tile_first[kNumClasses] = {};   // [n_inst] first tile of class c in the instance
+    int32_t tiles_total[kNumClasses] = {};
+    int32_t kmax[kNumClasses] = {};
+    int32_t* var_prefix = nullptr;           // [n_inst + 1]
+    int32_t vars_total = 0;
+    int32_t* slot_prefix = nullptr;          // [n_inst + 1] padded slots
+    int32_t slots_total = 0;
+    int32_t* chunk_prefix = nullptr;         // [n_inst + 1] lower-bound chunks
+    int32_t chunks_total = 0;
+    int32_t* objchunk_prefix = nullptr;      // [n_inst + 1]
+    int32_t objchunks_total = 0;
+    int32_t n_inst = 0;
+};
+
+struct SweepArgs {
+    const InstDev* insts;
+    const int32_t* prefix;  // [n_inst + 1] tiles of this class per instance
+    const int32_t* first;   // [n_inst] first tile of this class in the instance
+    int32_t n_inst;
+    int32_t total;
+    int32_t kstride;        // shared-memory kernels: per-layer stride (>= longest row)
+    int32_t flags;          // kMMAddT | kMMBoth
+};
+
+// CUDA-event timing of the update sweeps and the deferred-sum kernel
+struct Profiler {
+    bool on = false;
+    int64_t launches = 0;  // kernel launches of this instance (always counted)
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep, reduce;
+    cudaEvent_t take();
+    void record(bool is_sweep, cudaEvent_t a, cudaEvent_t b) { (is_sweep ? sweep : reduce).emplace_back(a, b); }
+    // sums and recycles the recorded pairs (the stream must be synchronised)
+    void drain(int64_t& n_sweep, double& ms_sweep, int64_t& n_reduce, double& ms_reduce);
+    void release();
+};
+
+struct LaunchCfg {
+    int warps_per_block = 4;  // sweep kernels
+    int num_sms = 152;
+    Profiler* prof = nullptr;
+    void count(int n = 1) const {
+        if (prof) prof->launches += n;
+    }
+};
+
+// maximum layers the shared-memory sweep kernels take for a width
+int smem_max_layers(int width);
+
+cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_init(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_addback(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_zero_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_round_test(const DevBatch& b, int round, double delta, uint64_t seed, const LaunchCfg& cfg,
+                              cudaStream_t s);
+cudaError_t launch_round_apply(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+
+// one full dual iteration (forward pass, deferred sums, backward pass,
+// deferred sums, lower bound) on every instance of the batch
+cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+
+}  // namespace fdog

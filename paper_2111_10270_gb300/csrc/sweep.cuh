@@ -1,0 +1,326 @@
+// Sweep kernel template (included by the per-width translation units).
+//
+// One warp per tile of 32 BDDs of one shape, one thread per BDD.  All
+// per-layer loads/stores of a warp are single 128-byte transactions
+// (interleaved slots); the shape template is read with warp-uniform loads.
+// Shortest-path labels of the direction opposite to the pass are recomputed
+// on chip at the start of each pass, so no per-node state goes to HBM: the
+// per-slot multipliers are the only state the sweeps stream.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+
+namespace fdog {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
+
+// largest instance index i with prefix[i] <= g (empty instances are skipped)
+__device__ __forceinline__ int find_inst(const int32_t* __restrict__ prefix, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int W>
+__device__ __forceinline__ void load_codes(const uint16_t* __restrict__ p, uint32_t (&c)[W]) {
+    if constexpr (W == 2) {
+        const uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
+        c[0] = u & 0xFFFFu; c[1] = u >> 16;
+    } else if constexpr (W == 4) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        c[0] = u.x & 0xFFFFu; c[1] = u.x >> 16; c[2] = u.y & 0xFFFFu; c[3] = u.y >> 16;
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 8; ++q) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + q);
+            c[8 * q + 0] = u.x & 0xFFFFu; c[8 * q + 1] = u.x >> 16;
+            c[8 * q + 2] = u.y & 0xFFFFu; c[8 * q + 3] = u.y >> 16;
+            c[8 * q + 4] = u.z & 0xFFFFu; c[8 * q + 5] = u.z >> 16;
+            c[8 * q + 6] = u.w & 0xFFFFu; c[8 * q + 7] = u.w >> 16;
+        }
+    }
+}
+
+// label of the successor with the given code: a node of the next layer, TOP (0) or BOT (inf)
+template <int W>
+__device__ __forceinline__ float pick(const float (&x)[W], uint32_t code) {
+    float r = (code == kCodeTop) ? 0.f : finf();
+#pragma unroll
+    for (int w = 0; w < W; ++w) r = (code == static_cast<uint32_t>(w)) ? x[w] : r;
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ void push(float (&x)[W], uint32_t code, float val) {
+#pragma unroll
+    for (int w = 0; w < W; ++w)
+        if (code == static_cast<uint32_t>(w)) x[w] = fminf(x[w], val);
+}
+
+// per-layer state of one BDD: registers for short rows, shared memory otherwise
+template <int W, bool REG>
+struct Store;
+
+template <int W>
+struct Store<W, true> {
+    float lam[kRegK], tb[kRegK], sp[kRegK][W];
+    __device__ __forceinline__ float& L(int t) { return lam[t]; }
+    __device__ __forceinline__ float& T(int t) { return tb[t]; }
+    __device__ __forceinline__ float& S(int t, int v) { return sp[t][v]; }
+};
+
+template <int W>
+struct Store<W, false> {
+    float* base;  // this lane's column of the warp's region
+    int stride;
+    __device__ __forceinline__ float& L(int t) { return base[t * kTile]; }
+    __device__ __forceinline__ float& T(int t) { return base[(stride + t) * kTile]; }
+    __device__ __forceinline__ float& S(int t, int v) { return base[(2 * stride + t * W + v) * kTile]; }
+};
+
+
+// Loops over layers.  With REG the trip count is the constant kRegK and the
+// loops unroll completely, so every index into Store is a compile-time
+// constant and the arrays stay in registers.
+#define FD_UP(t) _Pragma("unroll") for (int t = 0; t < (REG ? kRegK : k); ++t)
+#define FD_DOWN(t, tt) \
+    _Pragma("unroll") for (int tt = 0; tt < (REG ? kRegK : k); ++tt) \
+        if (const int t = (REG ? kRegK : k) - 1 - tt; t < k)
+
+template <int W, bool REG, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
+            if (I->ctl->done) continue;  // stopping rule met for this instance
+        }
+        const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
+        const ShapeDev sh = I->shapes[tile.shape];
+        const int k = sh.k;
+        const uint16_t* __restrict__ tpl = I->tpl + sh.tpl_off;
+        const bool valid = lane < tile.n_valid;
+        const float omega = I->omega;
+        const size_t base = static_cast<size_t>(tile.slot_base) + lane;
+        float* __restrict__ lam = I->lam;
+        const bool need_t = (MODE == kFwdUpdate || MODE == kBwdUpdate) || (a.flags & kMMAddT);
+
+        Store<W, REG> S;
+        if constexpr (!REG) {
+            S.base = smem + static_cast<size_t>(wib) * a.kstride * kTile * (2 + W) + lane;
+            S.stride = a.kstride;
+        }
+
+        // multipliers and deferred terms of every layer (coalesced per layer)
+        FD_UP(t) {
+            if (t >= k) break;
+            float l = 0.f, tb = 0.f;
+            if (valid) {
+                l = lam[base + static_cast<size_t>(t) * kTile];
+                if (need_t) tb = I->T[I->var[base + static_cast<size_t>(t) * kTile]];
+            }
+            if constexpr (MODE == kMinMarg || MODE == kEval) {
+                if (a.flags & kMMAddT) l += tb;
+            }
+            S.L(t) = l;
+            S.T(t) = tb;
+        }
+
+        float term = 0.f;  // this BDD's share of the lower bound
+        if constexpr (MODE == kFwdUpdate || MODE == kMinMarg || MODE == kEval) {
+            // SP(v, TOP) of every node at the current multipliers (Alg. 4 without updates)
+            float nx[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) nx[v] = finf();
+            FD_DOWN(t, tt) {
+                uint32_t c[W];
+                load_codes<W>(tpl + t * W, c);
+                const float lt = S.L(t);
+                float cur[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) cur[v] = fminf(pick<W>(nx, c[v] & 0xFFu), pick<W>(nx, c[v] >> 8) + lt);
+#pragma unroll
+                for (int v = 0; v < W; ++v) { S.S(t, v) = cur[v]; nx[v] = cur[v]; }
+            }
+            if constexpr (MODE == kEval) term = nx[0];
+        }
+
+        if constexpr (MODE == kFwdUpdate || MODE == kMinMarg) {
+            // ascending pass: SP(r, .) incrementally (Alg. 3) and Eq. 6 per layer
+            float f[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) f[v] = v == 0 ? 0.f : finf();
+            float negsum = 0.f, E = finf();
+            float* __restrict__ mm0 = I->mm0;
+            float* __restrict__ mm1 = I->mm1;
+            FD_UP(t) {
+                if (t >= k) break;
+                uint32_t c[W];
+                load_codes<W>(tpl + t * W, c);
+                const int tn = REG ? ((t + 1 < kRegK) ? t + 1 : t) : ((t + 1 < k) ? t + 1 : t);
+                float b[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) b[v] = S.S(tn, v);  // unused on the last layer (terminal codes)
+                float m0 = finf(), m1 = finf();
+#pragma unroll
+                for (int v = 0; v < W; ++v) {
+                    m0 = fminf(m0, f[v] + pick<W>(b, c[v] & 0xFFu));
+                    m1 = fminf(m1, f[v] + pick<W>(b, c[v] >> 8));
+                }
+                const float lt = S.L(t);
+                m1 += lt;
+                float lt_new = lt;
+                if constexpr (MODE == kFwdUpdate) {
+                    const float d = m1 - m0;
+                    lt_new = fmaf(-omega, d, lt) + S.T(t);  // Eq. 5
+                    S.L(t) = lt_new;
+                    negsum += fmaxf(-d, 0.f);
+                } else {
+                    if (valid) {
+                        const size_t p = base + static_cast<size_t>(t) * kTile;
+                        if (a.flags & kMMBoth) { mm0[p] = m0; mm1[p] = m1; }
+                        else mm0[p] = m1 - m0;
+                    }
+                }
+                float nf[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) nf[v] = finf();
+#pragma unroll
+                for (int v = 0; v < W; ++v) {
+                    const uint32_t lo = c[v] & 0xFFu, hi = c[v] >> 8;
+                    push<W>(nf, lo, f[v]);
+                    push<W>(nf, hi, f[v] + lt_new);
+                    E = fminf(E, lo == kCodeTop ? f[v] : finf());
+                    E = fminf(E, hi == kCodeTop ? f[v] + lt_new : finf());
+                }
+#pragma unroll
+                for (int v = 0; v < W; ++v) f[v] = nf[v];
+            }
+            term = E - omega * negsum;
+        }
+
+        if constexpr (MODE == kBwdUpdate) {
+            // SP(r, v) of every node at the current multipliers (Alg. 3 without updates)
+            float f[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) f[v] = v == 0 ? 0.f : finf();
+            FD_UP(t) {
+                if (t >= k) break;
+                uint32_t c[W];
+                load_codes<W>(tpl + t * W, c);
+                const float lt = S.L(t);
+                float nf[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) { S.S(t, v) = f[v]; nf[v] = finf(); }
+#pragma unroll
+                for (int v = 0; v < W; ++v) {
+                    push<W>(nf, c[v] & 0xFFu, f[v]);
+                    push<W>(nf, c[v] >> 8, f[v] + lt);
+                }
+#pragma unroll
+                for (int v = 0; v < W; ++v) f[v] = nf[v];
+            }
+            // descending pass: SP(., TOP) incrementally (Alg. 4) and Eq. 6 per layer
+            float b[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) b[v] = finf();
+            float negsum = 0.f;
+            FD_DOWN(t, tt) {
+                uint32_t c[W];
+                load_codes<W>(tpl + t * W, c);
+                float m0 = finf(), m1 = finf();
+#pragma unroll
+                for (int v = 0; v < W; ++v) {
+                    const float fv = S.S(t, v);
+                    m0 = fminf(m0, fv + pick<W>(b, c[v] & 0xFFu));
+                    m1 = fminf(m1, fv + pick<W>(b, c[v] >> 8));
+                }
+                const float lt = S.L(t);
+                m1 += lt;
+                const float d = m1 - m0;
+                const float lt_new = fmaf(-omega, d, lt) + S.T(t);  // Eq. 5
+                S.L(t) = lt_new;
+                negsum += fmaxf(-d, 0.f);
+                float nb[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) nb[v] = fminf(pick<W>(b, c[v] & 0xFFu), pick<W>(b, c[v] >> 8) + lt_new);
+#pragma unroll
+                for (int v = 0; v < W; ++v) b[v] = nb[v];
+            }
+            term = b[0] - omega * negsum;
+        }
+
+        if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
+            FD_UP(t) {
+                if (t >= k) break;
+                if (valid) lam[base + static_cast<size_t>(t) * kTile] = S.L(t);
+            }
+        }
+
+        // per-tile partial of the bound: compensated FP32 butterfly (all lanes end equal)
+        float s = valid ? term : 0.f, comp = 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float o = __shfl_xor_sync(kFull, s, off);
+            const float oc = __shfl_xor_sync(kFull, comp, off);
+            const float sum = s + o;
+            const float bp = sum - s;
+            const float err = (s - (sum - bp)) + (o - bp);
+            s = sum;
+            comp = comp + oc + err;
+        }
+        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] =
+            static_cast<double>(s) + static_cast<double>(comp);
+    }
+}
+
+#undef FD_UP
+#undef FD_DOWN
+
+}  // namespace dev
+
+// host-side dispatch of one width's instantiations (defined in sweep_w<W>.cu)
+template <int W>
+cudaError_t launch_sweep_width(bool reg, int mode, int blocks, int threads, size_t smem, cudaStream_t s,
+                               const SweepArgs& a);
+
+#define FDOG_DEFINE_SWEEP_WIDTH(W, HAS_REG)                                                                    \
+    template <>                                                                                                \
+    cudaError_t launch_sweep_width<W>(bool reg, int mode, int blocks, int threads, size_t smem, cudaStream_t s, \
+                                      const SweepArgs& a) {                                                    \
+        void (*fn)(SweepArgs) = nullptr;                                                                       \
+        if (HAS_REG && reg) {                                                                                  \
+            fn = mode == kFwdUpdate ? dev::sweep_kernel<W, HAS_REG, kFwdUpdate>                                \
+               : mode == kBwdUpdate ? dev::sweep_kernel<W, HAS_REG, kBwdUpdate>                                \
+               : mode == kMinMarg   ? dev::sweep_kernel<W, HAS_REG, kMinMarg>                                  \
+                                    : dev::sweep_kernel<W, HAS_REG, kEval>;                                    \
+        } else {                                                                                               \
+            fn = mode == kFwdUpdate ? dev::sweep_kernel<W, false, kFwdUpdate>                                  \
+               : mode == kBwdUpdate ? dev::sweep_kernel<W, false, kBwdUpdate>                                  \
+               : mode == kMinMarg   ? dev::sweep_kernel<W, false, kMinMarg>                                    \
+                                    : dev::sweep_kernel<W, false, kEval>;                                      \
+        }                                                                                                      \
+        if (smem > 48 * 1024) {                                                                                \
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                                 static_cast<int>(smem));                                      \
+            if (e != cudaSuccess) return e;                                                                    \
+        }                                                                                                      \
+        fn<<<blocks, threads, smem, s>>>(a);                                                                   \
+        return cudaGetLastError();                                                                             \
+    }
+
+}  // namespace fdog

@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, element by element.
+
+Tolerances: min-marginals |a-b| <= 1e-4 max(1,|a|,|b|), lower bounds
+|a-b| <= 1e-6 max(1,|a|); integer results (solutions, feasibility, sizes)
+bit-exact.  Two kinds of parity:
+  * evaluation parity: the oracle evaluates the GPU's own multipliers, so
+    only the FP32 evaluation error enters;
+  * trajectory parity: both run the same iteration schedule from scratch.
+"""
+import numpy as np
+import pytest
+
+import ilpgen
+from parity_util import LB_RTOL, MM_RTOL, lb_close, rel_err, slot_order
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2111_10270_gb300 import build as b
+
+    b.build()
+    import paper_2111_10270_gb300 as P
+
+    return P
+
+
+def gpu_instance(P, ilp, **kw):
+    kw.setdefault("tol", 0.0)
+    return P.Instance.from_ilp(ilp, **kw).build(0)
+
+
+# ----------------------------------------------------------------------------
+# the paper's examples
+# ----------------------------------------------------------------------------
+def test_fig3_min_marginals_exact(P, oracle_mod):
+    inst = gpu_instance(P, ilpgen.fig3_example())
+    var, row, m0, m1 = inst.min_marginals()
+    order = np.argsort(var)
+    assert np.array_equal(m0[order], [0, 0, 0, 0])
+    assert np.array_equal(m1[order], [3, 5, 3, 5])
+    assert inst.lower_bound() == (0.0, 0.0)
+
+
+def test_fig2_bound_stays_at_optimum_and_rounds_at_once(P):
+    inst = gpu_instance(P, ilpgen.fig2_example())
+    for _ in range(30):
+        n, lb = inst.iterate(1)
+        assert n == 1 and lb == -5.0
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    assert rc == 0 and rounds == 0 and list(x) == [1, 0, 0, 0] and obj == -5.0 and feas
+
+
+def test_fig2_first_iteration_matches_oracle_exactly(P, oracle_mod):
+    ilp = ilpgen.fig2_example()
+    inst = gpu_instance(P, ilp)
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    inst.iterate(1)
+    orc.iterate(1)
+    var, row, lam = inst.multipliers()
+    hi, lo, _, _ = orc.state()
+    perm = slot_order(orc, var, row)
+    assert np.array_equal(lam[perm].astype(np.float64), hi - lo)  # dyadic values: exact in FP32
+
+
+# ----------------------------------------------------------------------------
+# trajectory and evaluation parity
+# ----------------------------------------------------------------------------
+def trajectory(P, oracle_mod, ilp, iters, omega=0.5):
+    inst = gpu_instance(P, ilp, omega=omega)
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    gl = np.array([inst.iterate(1)[1] for _ in range(iters)])
+    ol = orc.iterate(iters, omega)
+    return inst, orc, gl, ol
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tiny_mrf_trajectory_parity(P, oracle_mod, seed):
+    g = ilpgen.mrf_grid(8, 8, 3, seed)
+    inst, orc, gl, ol = trajectory(P, oracle_mod, g, 200)
+    assert np.all(np.diff(gl) >= -1e-5 * max(1.0, abs(gl[-1])))
+    bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t])]
+    assert not bad, (bad[:5], gl[bad[0]], ol[bad[0]])
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    hi, lo, _, _ = orc.state()
+    perm = slot_order(orc, var, row)
+    # both sides report min-marginals of the plain multipliers lambda = hi - lo
+    assert rel_err(m0[perm], om0).max() <= MM_RTOL
+    assert rel_err(m1[perm], om1).max() <= MM_RTOL
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    _, lbf = inst.lower_bound()
+    _, olbf = orc.lower_bounds()
+    assert lb_close(lbf, olbf)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tiny_mrf_evaluation_parity(P, oracle_mod, seed):
+    """The oracle evaluates the GPU's multipliers: min-marginals and the bound
+    of the finalised (dual-feasible) state."""
+    g = ilpgen.mrf_grid(8, 8, 3, 10 + seed)
+    inst = gpu_instance(P, g)
+    inst.iterate(57)
+    inst.finalize()
+    var, row, lam = inst.multipliers()
+    orc = oracle_mod.Problem.from_ilp(g)
+    perm = slot_order(orc, var, row)
+    orc.set_state(lam[perm].astype(np.float64))
+    om0, om1 = orc.min_marginals()
+    var2, row2, m0, m1 = inst.min_marginals()
+    perm2 = slot_order(orc, var2, row2)
+    assert rel_err(m0[perm2], om0).max() <= MM_RTOL
+    assert rel_err(m1[perm2], om1).max() <= MM_RTOL
+    run, fea = inst.lower_bound()
+    orun, ofea = orc.lower_bounds()
+    assert lb_close(run, orun) and lb_close(fea, ofea)
+    # dual feasibility after the add-back: sum_j lambda^j_i = c_i (FP32)
+    s = np.bincount(var, lam.astype(np.float64), minlength=g.n_vars)
+    inb = np.bincount(var, minlength=g.n_vars) > 0
+    assert np.abs(s - g.cost)[inb].max() <= 1e-5 * max(1.0, np.abs(g.cost).max())
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_ilp_trajectory_parity(P, oracle_mod, seed):
+    ilp = ilpgen.random_ilp(40, 30, 700 + seed, max_row=9, max_coef=3)
+    omega = [0.5, 0.25, 1.0, 0.7][seed % 4]
+    inst, orc, gl, ol = trajectory(P, oracle_mod, ilp, 60, omega)
+    assert all(lb_close(a, b) for a, b in zip(gl, ol)), np.max(np.abs(gl - ol))
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+
+
+def test_wide_and_long_rows_parity(P, oracle_mod):
+    """Shapes of every kernel class: widths 2 / 4 / 8 / 16 with short and long
+    rows, ragged tiles."""
+    rng = np.random.default_rng(5)
+    rb = ilpgen._RowBuilder()
+    n = 60
+    for j in range(70):
+        k = int(rng.integers(2, 30))
+        cols = np.sort(rng.choice(n, k, replace=False))
+        kind = j % 5
+        if kind == 0:
+            rb.add(cols, [1] * k, -1, int(rng.integers(1, min(k, 14))))     # cardinality: width up to 15
+        elif kind == 1:
+            rb.add(cols, [1] * k, 0, 1)                                     # simplex
+        elif kind == 2:
+            a = rng.integers(1, 3, k) * rng.choice([-1, 1], k)
+            rb.add(cols, a, -1, int(np.abs(a).sum() // 3))
+        elif kind == 3:
+            rb.add(cols[:5], [1, 1, -1, 1, -1], 0, 0)
+        else:
+            rb.add(cols[:3], [2, -1, -1], 1, 0)
+    ilp = rb.finish(n, rng.standard_normal(n), "classes")
+    inst = P.Instance.from_ilp(ilp, tol=0.0)
+    inst.plan()
+    inst.build(0)
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    gl = np.array([inst.iterate(1)[1] for _ in range(40)])
+    ol = orc.iterate(40)
+    assert all(lb_close(a, b) for a, b in zip(gl, ol)), np.max(np.abs(gl - ol))
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+
+
+# ----------------------------------------------------------------------------
+# rounding
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(3))
+def test_tiny_mrf_rounding_parity(P, oracle_mod, seed):
+    g = ilpgen.mrf_grid(8, 8, 3, 20 + seed, potts_max=1.5)
+    inst = gpu_instance(P, g)
+    orc = oracle_mod.Problem.from_ilp(g)
+    inst.iterate(200)
+    orc.iterate(200)
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    r = orc.round()
+    assert rc == 0 and feas and g.feasible(x)
+    assert abs(obj - g.objective(x)) <= 1e-9 * max(1.0, abs(obj))
+    _, lbf = orc.lower_bounds()
+    assert obj >= lbf - 1e-6 * max(1.0, abs(lbf))  # a feasible point is never below the bound
+    scale = max(1.0, np.abs(g.cost).max())
+    if r["margin"] > 1e-3 * scale:
+        assert np.array_equal(x, r["x"]) and rounds == r["rounds"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_ilp_rounding_feasible(P, oracle_mod, seed):
+    ilp = ilpgen.random_ilp(30, 25, 900 + seed, max_row=5, max_coef=1)
+    inst = gpu_instance(P, ilp, max_rounds=300)
+    inst.iterate(50)
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    orc.iterate(50)
+    r = orc.round(max_rounds=300)
+    if rc == 0:
+        assert feas == ilp.feasible(x)
+        assert feas
+    if r["status"] == 0 and r["margin"] > 1e-3 * max(1.0, np.abs(ilp.cost).max()):
+        assert rc == 0 and np.array_equal(x, r["x"])
+
+
+# ----------------------------------------------------------------------------
+# edge cases, determinism, checkpoint
+# ----------------------------------------------------------------------------
+def test_instance_without_rows(P):
+    c = np.array([1.0, -2.0, 0.5, -0.25])
+    ilp = ilpgen.ILP(4, c, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32),
+                     np.zeros(0, np.int8), np.zeros(0, np.int64))
+    inst = gpu_instance(P, ilp)
+    n, lb = inst.iterate(5)
+    assert lb == -2.25
+    assert inst.lower_bound() == (-2.25, -2.25)
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    assert list(x) == [0, 1, 0, 1] and obj == -2.25 and feas
+
+
+def test_presolve_fixed_variables_on_gpu(P, oracle_mod):
+    rb = ilpgen._RowBuilder()
+    rb.add([0, 1], [1, 1], 0, 2)
+    rb.add([1, 2], [1, 1], -1, 1)
+    rb.add([3, 4, 5], [1, -1, 1], 0, 1)
+    ilp = rb.finish(7, [1.0, 2.0, -3.0, -1.0, 0.5, 0.75, -0.25], "forced")
+    inst = gpu_instance(P, ilp)
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    assert np.array_equal(inst.fixed_vars(), orc.fixed())
+    gl = [inst.iterate(1)[1] for _ in range(20)]
+    ol = orc.iterate(20)
+    assert all(lb_close(a, b) for a, b in zip(gl, ol))
+    rc, _ = inst.primal_round()
+    x, obj, feas = inst.solution()
+    assert rc == 0 and feas and ilp.feasible(x)
+
+
+def test_runs_are_bitwise_deterministic(P):
+    g = ilpgen.mrf_grid(16, 16, 4, 3)
+    outs = []
+    for _ in range(2):
+        inst = gpu_instance(P, g)
+        lbs = [inst.iterate(1)[1] for _ in range(30)]
+        _, _, lam = inst.multipliers()
+        outs.append((lbs, lam.tobytes()))
+    assert outs[0] == outs[1]
+
+
+def test_block_size_does_not_change_results(P):
+    g = ilpgen.mrf_grid(16, 16, 3, 4)
+    res = []
+    for bt in (64, 128, 256):
+        inst = gpu_instance(P, g, block_threads=bt)
+        inst.iterate(25)
+        _, _, lam = inst.multipliers()
+        res.append((inst.lower_bound(), lam.tobytes()))
+    assert res[0] == res[1] == res[2]
+
+
+def test_checkpoint_resume_is_bit_identical(P):
+    g = ilpgen.mrf_grid(12, 12, 3, 5)
+    a = gpu_instance(P, g)
+    a.iterate(30)
+    blob = a.export_state()
+    a.iterate(20)
+    _, _, lam_a = a.multipliers()
+    lb_a = a.lower_bound()
+    b = gpu_instance(P, g)
+    b.import_state(blob)
+    b.iterate(20)
+    _, _, lam_b = b.multipliers()
+    assert lam_a.tobytes() == lam_b.tobytes() and lb_a == b.lower_bound()
+    c = gpu_instance(P, ilpgen.mrf_grid(12, 12, 3, 6))
+    with pytest.raises(P.FdogError):
+        c.import_state(blob[:-8])
+
+
+def test_early_stopping_rule(P, oracle_mod):
+    g = ilpgen.mrf_grid(8, 8, 3, 7)
+    inst = gpu_instance(P, g, tol=1e-4, window=10, min_iters=20)
+    n, lb = inst.iterate(2000)
+    assert 20 <= n < 2000
+    orc = oracle_mod.Problem.from_ilp(g)
+    tr = orc.iterate(n + 5)
+    # the oracle's bound satisfies the same rule within a couple of iterations of the stop
+    stops = [t for t in range(20, len(tr)) if t + 1 > 10 and tr[t] - tr[t - 10] <= 1e-4 * max(1.0, abs(tr[t]))]
+    assert stops and abs((stops[0] + 1) - n) <= 2
+    assert inst.iterate(10)[0] == 0  # stays stopped
+
+
+# ----------------------------------------------------------------------------
+# full-size workload (512 x 512 grid, 4 labels) in the benchmark's launch configuration
+# ----------------------------------------------------------------------------
+def test_large_mrf_evaluation_parity_full_size(P, oracle_mod):
+    g = ilpgen.mrf_grid(512, 512, 4, 1, potts_max=2.0)
+    inst = gpu_instance(P, g)
+    info = inst.info()
+    assert (info["n_vars"], info["n_bdds"], info["n_slots"], info["n_nodes"]) == (9420800, 4448256, 21979136,
+                                                                                    39510016)
+    n, lb = inst.iterate(25)
+    assert n == 25
+    run, fea = inst.lower_bound()
+    inst.finalize()
+    var, row, lam = inst.multipliers()
+    orc = oracle_mod.Problem.from_ilp(g)
+    perm = slot_order(orc, var, row)
+    orc.set_state(lam[perm].astype(np.float64))
+    orun, ofea = orc.lower_bounds()
+    assert lb_close(fea, ofea, LB_RTOL), (fea, ofea)
+    # min-marginals of every slot at the finalised multipliers
+    var2, row2, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm2 = slot_order(orc, var2, row2)
+    assert rel_err(m0[perm2], om0).max() <= MM_RTOL
+    assert rel_err(m1[perm2], om1).max() <= MM_RTOL
+    assert run <= fea + 1e-6 * abs(fea)

@@ -74,6 +74,10 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *   seed = 0                   seed of the counter-based perturbation draws
  *   block_threads = 0          threads per CTA for the sweep kernels;
  *                              0 = use the built-in autotuner
+ *   jit = 0                    shape-specialised sweep kernels, compiled at
+ *                              build time with NVRTC for rows of width <= 4 and
+ *                              length <= 16: 0 = use them when available
+ *                              (falls back to the generic kernels), -1 = never
  */
 typedef struct {
     double omega;
@@ -86,7 +90,8 @@ typedef struct {
     int32_t max_rounds;
     uint64_t seed;
     int32_t block_threads;
-    int32_t reserved[7];
+    int32_t jit;
+    int32_t reserved[6];
 } fdog_params;
 
 /* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */
@@ -126,6 +131,16 @@ int fdog_plan(fdog_instance* inst, int64_t* device_bytes);
  * presolve gives *k = 0.  FDOG_ESTATE if not planned.
  */
 int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed);
+
+/*
+ * Which sweep kernels a planned instance uses: *jit_shapes distinct shapes
+ * with shape-specialised kernels, covering *jit_tiles tiles of 32 BDDs;
+ * *static_tiles tiles run the generic kernels.  If the specialised kernels
+ * could not be compiled, `note` (capacity note_cap, may be NULL) receives the
+ * reason.  Any pointer may be NULL.  FDOG_ESTATE if not planned.
+ */
+int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
+                     char* note, int32_t note_cap);
 int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes, int32_t* vars, int32_t* lstart,
                  int32_t* lo, int32_t* hi);
 

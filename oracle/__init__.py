@@ -56,6 +56,7 @@ def _load():
             "orc_create": (i32, [i32, ptr, i32, ptr, ptr, ptr, ptr, ptr, ctypes.POINTER(P)]),
             "orc_destroy": (None, [P]),
             "orc_lower_bounds": (i32, [P, f64, ptr, ptr]),
+            "orc_energies": (i32, [P, ptr]),
             "orc_pass": (i32, [P, i32, f64, ptr]),
             "orc_iterate": (i32, [P, i32, f64, ptr]),
             "orc_addback": (i32, [P, f64]),
@@ -222,6 +223,12 @@ class Problem:
         a, b = ctypes.c_double(), ctypes.c_double()
         self._lib.orc_lower_bounds(self._h, omega, ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value
+
+    def energies(self):
+        """Lifted energy E(hi^j, lo^j) of every BDD at the current state."""
+        E = np.zeros(max(self.m, 1))
+        self._lib.orc_energies(self._h, _p(E))
+        return E[:self.m]
 
     def min_marginals(self):
         m0 = np.zeros(self.S)

@@ -600,6 +600,14 @@ int orc_lower_bounds(const orc_problem *p, double omega, double *lb_running, dou
     return ORC_OK;
 }
 
+/* E(hi^j, lo^j) of every BDD at the current state (the terms of the running bound) */
+int orc_energies(const orc_problem *p, double *E) {
+    double *scr = malloc(sizeof(double) * max_nodes(p));
+    for (int j = 0; j < p->m; ++j) E[j] = bdd_energy(p, j, p->lo + p->slot0[j], p->hi + p->slot0[j], scr);
+    free(scr);
+    return ORC_OK;
+}
+
 /* one pass; exposed so that tests can check Prop. 1 after every pass */
 int orc_pass(orc_problem *p, int forward, double omega, double *M_out) {
     if (!(omega > 0 && omega <= 1)) return ORC_EINVAL;

@@ -16,8 +16,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfastdog.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["bdd_build.cpp", "kernels.cu", "sweep_w2.cu", "sweep_w4.cu", "sweep_w8.cu", "sweep_w16.cu", "api.cu",
-           "state.cu"]
+SOURCES = ["bdd_build.cpp", "jit.cpp", "kernels.cu", "sweep_w2.cu", "sweep_w4.cu", "sweep_w8.cu", "sweep_w16.cu",
+           "api.cu", "state.cu"]
+GEN = os.path.join(BUILD, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +33,23 @@ def nvcc_path() -> str:
 
 
 def _flags():
-    return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I", INCLUDE, "-I", CSRC]
+    return ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I", INCLUDE, "-I", CSRC, "-I", GEN]
+
+
+def write_jit_sources():
+    """Embeds the device-ABI block of fdog_internal.h and the kernel skeleton
+    as string literals for the shape-specialised (NVRTC) kernels."""
+    hdr = open(os.path.join(CSRC, "fdog_internal.h")).read()
+    abi = hdr[hdr.index("// <jit-abi>"):hdr.index("// </jit-abi>")]
+    skel = open(os.path.join(CSRC, "jit_skeleton.cuh")).read()
+    os.makedirs(GEN, exist_ok=True)
+    text = ("// generated by build.py from fdog_internal.h and jit_skeleton.cuh\n"
+            f'static const char* kJitAbi = R"FDOGJIT({abi})FDOGJIT";\n'
+            f'static const char* kJitSkeleton = R"FDOGJIT({skel})FDOGJIT";\n')
+    path = os.path.join(GEN, "jit_sources.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
 
 
 def _deps():
@@ -53,6 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if not force and up_to_date():
         return LIB
     nvcc = nvcc_path()
+    write_jit_sources()
     obj_dir = os.path.join(BUILD, "obj")
     os.makedirs(obj_dir, exist_ok=True)
     flags = _flags()
@@ -76,7 +94,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if log.strip():
                 sys.stderr.write(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart_static", "-lnvrtc", "-lrt", "-lpthread",
+           "-ldl", "-Xlinker", "-rpath=" + os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

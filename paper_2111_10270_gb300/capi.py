@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
         ("max_rounds", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("block_threads", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("jit", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -58,6 +59,8 @@ SIGNATURES = {
     "fdog_create": (ctypes.c_int, [_i32, _P, _i32, _P, _P, _P, _P, _P, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "fdog_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i64)]),
     "fdog_fixed_vars": (ctypes.c_int, [_P, _P]),
+    "fdog_kernel_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                        ctypes.c_char_p, _i32]),
     "fdog_row_bdd": (ctypes.c_int, [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P, _P, _P, _P]),
     "fdog_build_bdds": (ctypes.c_int, [_P, _i32, _P]),
     "fdog_reset_dual": (ctypes.c_int, [_P]),
@@ -171,6 +174,14 @@ class Instance:
         b = _i64()
         self._check(self._L.fdog_plan(self._h, ctypes.byref(b)), "fdog_plan")
         return b.value
+
+    def kernel_plan(self):
+        js, jt, st = _i32(), _i64(), _i64()
+        note = ctypes.create_string_buffer(2048)
+        self._check(self._L.fdog_kernel_plan(self._h, ctypes.byref(js), ctypes.byref(jt), ctypes.byref(st), note,
+                                             2048), "fdog_kernel_plan")
+        return {"jit_shapes": js.value, "jit_tiles": jt.value, "static_tiles": st.value,
+                "note": note.value.decode(errors="replace")}
 
     def fixed_vars(self):
         f = np.zeros(self.n_vars, np.int8)

@@ -74,6 +74,7 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.cost), sizeof(double) * sz(n)},
         {reinterpret_cast<void**>(&a.csr_off), sizeof(int32_t) * static_cast<size_t>(n + 1)},
         {reinterpret_cast<void**>(&a.csr_pos), sizeof(int32_t) * sz(d.n_slots)},
+        {reinterpret_cast<void**>(&a.vrec), 4 * sizeof(int32_t) * sz(n)},
         {reinterpret_cast<void**>(&a.tile_lb), sizeof(double) * sz(nt)},
         {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
         {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
@@ -88,13 +89,20 @@ size_t arena_size(const fdog_instance* inst) {
     return total;
 }
 
+std::vector<int> jit_ids(const fdog_instance* inst) {
+    std::vector<int> ids;
+    for (const ShapeDev& s : inst->dec.shape_dev)
+        if (s.jit >= 0) ids.push_back(s.jit);
+    return ids;
+}
+
 int plan(fdog_instance* inst) {
     if (inst->planned) return FDOG_OK;
     int rc;
     try {
         rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
-                                 inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(), inst->dec,
-                                 inst->last_error);
+                                 inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(),
+                                 inst->params.jit >= 0 && !inst->jit_failed, inst->dec, inst->last_error);
     } catch (const std::bad_alloc&) {
         rc = FDOG_ENOMEM;
     } catch (...) {
@@ -106,6 +114,16 @@ int plan(fdog_instance* inst) {
             inst->last_error = "row longer than the shared-memory sweep kernels take";
             return FDOG_EUNSUPPORTED;
         }
+    std::vector<int> ids = jit_ids(inst);
+    if (!ids.empty()) {
+        std::string why;
+        if (jit_compile(ids, why) != FDOG_OK) {
+            // shape-specialised kernels unavailable: plan again for the generic kernels only
+            inst->jit_note = why;
+            inst->jit_failed = true;
+            return plan(inst);
+        }
+    }
     inst->planned = true;
     return FDOG_OK;
 }
@@ -149,6 +167,7 @@ int allocate_and_upload(fdog_instance* inst) {
     h.C = a.C;
     h.csr_off = a.csr_off;
     h.csr_pos = a.csr_pos;
+    h.vrec = a.vrec;
     h.cost = a.cost;
     h.pert = a.pert;
     h.x = a.x;
@@ -170,6 +189,7 @@ int allocate_and_upload(fdog_instance* inst) {
     b = DevBatch();
     b.insts = a.inst;
     b.n_inst = 1;
+    b.jit = inst->jit;
     int q = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         pre[q] = 0;
@@ -208,6 +228,7 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.cost, inst->cost.data(), sizeof(double) * n);
     up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
     up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
+    up(a.vrec, d.vrec.data(), sizeof(int32_t) * d.vrec.size());
     up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
     if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
     return FDOG_OK;
@@ -388,6 +409,17 @@ int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream) {
     inst->stream = static_cast<cudaStream_t>(cuda_stream);
     int rc = plan(inst);
     if (rc != FDOG_OK) return rc;
+    const std::vector<int> ids = jit_ids(inst);
+    if (!ids.empty()) {
+        std::string why;
+        if (jit_kernels(ids, inst->jit, why) != FDOG_OK) {
+            // shape-specialised kernels unavailable: plan again for the generic kernels
+            inst->jit_note = why;
+            inst->jit_failed = true;
+            inst->planned = false;
+            if ((rc = plan(inst)) != FDOG_OK) return rc;
+        }
+    }
     cudaDeviceProp prop;
     e = cudaGetDeviceProperties(&prop, device);
     if (e != cudaSuccess) return fail_cuda(inst, e, "device properties");
@@ -411,6 +443,24 @@ int fdog_plan(fdog_instance* inst, int64_t* device_bytes) {
     int rc = plan(inst);
     if (rc != FDOG_OK) return rc;
     if (device_bytes) *device_bytes = static_cast<int64_t>(arena_size(inst));
+    return FDOG_OK;
+}
+
+int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
+                     char* note, int32_t note_cap) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->planned) return FDOG_ESTATE;
+    const Decomposition& d = inst->dec;
+    if (jit_shapes) *jit_shapes = static_cast<int32_t>(jit_ids(inst).size());
+    const int64_t jt = d.cls_tile_begin[kJitClass + 1] - d.cls_tile_begin[kJitClass];
+    if (jit_tiles) *jit_tiles = jt;
+    if (static_tiles) *static_tiles = static_cast<int64_t>(d.tiles.size()) - jt;
+    if (note && note_cap > 0) {
+        const std::string& s = inst->jit_note;
+        const size_t n = std::min<size_t>(s.size(), static_cast<size_t>(note_cap - 1));
+        std::memcpy(note, s.data(), n);
+        note[n] = '\0';
+    }
     return FDOG_OK;
 }
 

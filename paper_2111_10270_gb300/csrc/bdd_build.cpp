@@ -162,7 +162,7 @@ std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) 
 
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        Decomposition& out, std::string& err) {
+                        bool use_jit, Decomposition& out, std::string& err) {
     out = Decomposition();
     out.fixed.assign(n_vars, -1);
 
@@ -246,6 +246,7 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         if (shape_of_an[id] < 0) {
             const HostShape& s = analyses[id].shape;
             int cls = class_of(s.width, s.k);
+            if (use_jit && s.width <= kJitMaxW && s.k <= kJitMaxK) cls = kJitClass;
             if (cls < 0 || (!class_is_reg(cls) && s.k > kMaxLayersSmem)) {
                 err = "row " + std::to_string(j) + ": BDD width " + std::to_string(s.width) + " / length " +
                       std::to_string(s.k) + " exceeds the sweep kernels' limits";
@@ -283,7 +284,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         const HostShape& h = out.shapes[s];
         int W = class_width(out.shape_cls[s]);
         while (out.tpl.size() % 8) out.tpl.push_back(0);  // 16-byte aligned vector loads
-        ShapeDev d{h.k, static_cast<int32_t>(out.tpl.size()), W, 0};
+        const int jit = out.shape_cls[s] == kJitClass ? jit_register_shape(h) : -1;
+        ShapeDev d{h.k, static_cast<int32_t>(out.tpl.size()), W, jit};
         out.shape_dev[s] = d;
         for (int t = 0; t < h.k; ++t) {
             int b = h.lstart[t], e = h.lstart[t + 1];
@@ -348,6 +350,16 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
     for (int64_t p = 0; p < slot; ++p)
         if (out.var[p] >= 0) out.csr_pos[fill[out.var[p]]++] = static_cast<int32_t>(p);
+    // per-variable records: the first two slots inline, so that most variables
+    // need one record load before their multipliers can be fetched
+    out.vrec.resize(4 * static_cast<size_t>(n_vars));
+    for (int32_t i = 0; i < n_vars; ++i) {
+        const int32_t b = out.csr_off[i], c = out.csr_off[i + 1] - b;
+        out.vrec[4 * i + 0] = c > 0 ? out.csr_pos[b] : -1;
+        out.vrec[4 * i + 1] = c > 1 ? out.csr_pos[b + 1] : -1;
+        out.vrec[4 * i + 2] = b;
+        out.vrec[4 * i + 3] = c;
+    }
     return FDOG_OK;
 }
 

@@ -29,7 +29,11 @@ constexpr int kWidths[4] = {2, 4, 8, 16};
 constexpr int kNumWidths = 4;
 constexpr int kMaxWidth = 16;
 constexpr int kMaxLayersSmem = 256;  // longest row the shared-memory kernels take
-constexpr int kNumClasses = 2 * kNumWidths;  // (width index) x (register | smem)
+constexpr int kNumStaticClasses = 2 * kNumWidths;  // (width index) x (register | smem)
+constexpr int kJitClass = kNumStaticClasses;         // shape-specialised kernels
+constexpr int kNumClasses = kNumStaticClasses + 1;
+constexpr int kJitMaxK = 16;                         // rows the shape-specialised code takes
+constexpr int kJitMaxW = 4;
 
 inline int class_of(int width, int k) {
     int wi = 0;
@@ -37,14 +41,15 @@ inline int class_of(int width, int k) {
     if (wi == kNumWidths) return -1;
     return wi * 2 + ((k <= kRegK && kWidths[wi] <= kRegW) ? 0 : 1);
 }
-inline int class_width(int cls) { return kWidths[cls / 2]; }
-inline bool class_is_reg(int cls) { return (cls % 2) == 0; }
+inline int class_width(int cls) { return cls == kJitClass ? kJitMaxW : kWidths[cls / 2]; }
+inline bool class_is_reg(int cls) { return cls == kJitClass || (cls % 2) == 0; }
 
+// <jit-abi>  (this block is also compiled into the shape-specialised kernels)
 struct ShapeDev {
     int32_t k;        // layers (= variables of the row)
     int32_t tpl_off;  // offset (in uint16 units) of the template: k * W entries
     int32_t width;    // W of its class
-    int32_t pad;
+    int32_t jit;      // process-wide id of the shape-specialised code, -1 if none
 };
 
 struct TileDev {
@@ -54,11 +59,11 @@ struct TileDev {
     int32_t bdd_base;  // index of lane 0's BDD in the instance's BDD order
 };
 
-constexpr int kLbRing = 64;
+#define FDOG_LB_RING 64
 
 // Device-resident control block of one instance.
 struct InstCtl {
-    double lb_ring[kLbRing];  // running lower bound after iteration t at [t % kLbRing]
+    double lb_ring[FDOG_LB_RING];  // running lower bound after iteration t at [t % kLbRing]
     double lb_last;           // running lower bound after the last iteration
     double lb_eval;           // result of the last evaluation reduction
     double objective;         // c^T x of the last rounding (without presolve constants)
@@ -88,6 +93,7 @@ struct InstDev {
     float* C;                // [n] target sum_j lambda^j_i (= c_i, perturbed by rounding)
     const int32_t* csr_off;  // [n + 1]
     const int32_t* csr_pos;  // [slots] padded slot positions of each variable, ascending
+    const int32_t* vrec;     // [4 n] {first slot, second slot or -1, csr_off, |J_i|}, 16-byte aligned
     const double* cost;      // [n]
     float* pert;             // [n] rounding perturbation of this round
     uint8_t* x;              // [n] rounded solution
@@ -103,6 +109,19 @@ struct InstDev {
     float pad0;
     double const_lb;
 };
+
+struct SweepArgs {
+    const InstDev* insts;
+    const int32_t* prefix;  // [n_inst + 1] tiles of this class per instance
+    const int32_t* first;   // [n_inst] first tile of this class in the instance
+    int32_t n_inst;
+    int32_t total;
+    int32_t kstride;        // shared-memory kernels: per-layer stride (>= longest row)
+    int32_t flags;          // evaluate at lambda + T (1) | write m0 and m1 (2)
+};
+
+// </jit-abi>
+constexpr int kLbRing = FDOG_LB_RING;
 
 // ---------------------------------------------------------------------------
 // host-side decomposition
@@ -133,6 +152,7 @@ struct Decomposition {
     std::vector<int32_t> cls_tile_begin;  // kNumClasses + 1 (tiles sorted by class)
     std::vector<int32_t> var;      // padded slots
     std::vector<int32_t> csr_off, csr_pos;
+    std::vector<int32_t> vrec;     // 4 ints per variable: {first slot, second slot or -1, csr_off, count}
     std::vector<ShapeDev> shape_dev;
     std::vector<uint16_t> tpl;
     int64_t n_bdds = 0, n_slots = 0, n_nodes = 0, slots_pad = 0;
@@ -144,7 +164,19 @@ struct Decomposition {
 // Returns an FDOG_* status.
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        Decomposition& out, std::string& err);
+                        bool use_jit, Decomposition& out, std::string& err);
+
+// shape-specialised code (jit.cpp): process-wide shape registry and kernels
+int jit_register_shape(const HostShape& s);  // id of the shape's structure
+struct JitKernels {
+    const void* fn[4] = {nullptr, nullptr, nullptr, nullptr};  // per sweep mode
+};
+// host-only NVRTC compile of the module for the given shape ids (cached)
+int jit_compile(const std::vector<int>& ids, std::string& err);
+// compiles if needed and loads the module; empty ids -> no kernels
+int jit_kernels(const std::vector<int>& ids, JitKernels& out, std::string& err);
+// the generated CUDA source of the module (for inspection)
+std::string jit_source(const std::vector<int>& ids);
 
 // BDD of { x in {0,1}^k : lo_bound <= sum a_t x_t <= hi_bound } (either bound optional).
 int build_row_shape(const std::vector<int64_t>& a, bool has_lo, int64_t lo_bound, bool has_hi, int64_t hi_bound,

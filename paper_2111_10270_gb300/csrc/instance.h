@@ -31,6 +31,7 @@ struct DevArrays {
     double* cost = nullptr;
     int32_t* csr_off = nullptr;
     int32_t* csr_pos = nullptr;
+    int32_t* vrec = nullptr;
     double* tile_lb = nullptr;
     double* chunk_lb = nullptr;
     double* obj_chunk = nullptr;
@@ -64,6 +65,9 @@ struct fdog_instance {
     fdog::LaunchCfg cfg;
     fdog::InstCtl* host_ctl = nullptr;  // pinned
     fdog::Profiler prof;
+    fdog::JitKernels jit;     // shape-specialised kernels of this instance's shapes
+    bool jit_failed = false;  // NVRTC unavailable or failed: generic kernels only
+    std::string jit_note;
 
     // host-side view of the dual state
     bool pending_T = false;  // deferred differences of the last pass not yet added back

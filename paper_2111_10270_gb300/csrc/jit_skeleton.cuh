@@ -1,0 +1,60 @@
+// Skeleton of the shape-specialised sweep kernels.  This file is not compiled
+// by nvcc: the build embeds it as text, and at plan time jit.cpp appends the
+// generated per-shape functions and dispatch tables and compiles the result
+// for sm_103a with NVRTC.
+//
+// The tile loop, instance lookup and per-tile bound reduction are the same as
+// in the static sweep kernels (sweep.cuh); only the per-BDD work differs: it
+// is straight-line code for one known shape, with every successor choice
+// resolved when the code was generated, so a thread spends its instructions
+// on the min-plus arithmetic itself.
+
+#define FDOG_INF __int_as_float(0x7f800000)
+#define FDOG_FULL 0xffffffffu
+
+__device__ __forceinline__ int fdog_find_inst(const int32_t* __restrict__ prefix, int n, int g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// MODE: 0 ascending pass with updates, 1 descending pass with updates,
+//       2 min-marginals, 3 energies only
+template <int MODE>
+__device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        const int ii = fdog_find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        if (MODE <= 1 && I->ctl->done) continue;
+        const int ti = __ldg(a.first + ii) + (g - __ldg(a.prefix + ii));
+        const TileDev tile = I->tiles[ti];
+        const int jit = I->shapes[tile.shape].jit;
+        const bool valid = lane < tile.n_valid;
+        const size_t base = (size_t)tile.slot_base + lane;
+        float term = 0.f;
+        FDOG_DISPATCH(MODE)
+        float s = valid ? term : 0.f, comp = 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float o = __shfl_xor_sync(FDOG_FULL, s, off);
+            const float oc = __shfl_xor_sync(FDOG_FULL, comp, off);
+            const float sum = s + o;
+            const float bp = sum - s;
+            const float err = (s - (sum - bp)) + (o - bp);
+            s = sum;
+            comp = comp + oc + err;
+        }
+        if (lane == 0) I->tile_lb[ti] = (double)s + (double)comp;
+    }
+}
+
+extern "C" __global__ void __launch_bounds__(256) fdog_jit_fwd(SweepArgs a) { fdog_jit_sweep<0>(a); }
+extern "C" __global__ void __launch_bounds__(256) fdog_jit_bwd(SweepArgs a) { fdog_jit_sweep<1>(a); }
+extern "C" __global__ void __launch_bounds__(256) fdog_jit_mm(SweepArgs a) { fdog_jit_sweep<2>(a); }
+extern "C" __global__ void __launch_bounds__(256) fdog_jit_eval(SweepArgs a) { fdog_jit_sweep<3>(a); }

@@ -35,20 +35,27 @@ struct FlatArgs {
 // T_i = (C_i - sum_j lambda^j_i) / |J_i|.  Right after a pass, Prop. 1 gives
 // sum_j lambda^j_i + omega sum_j M_ij = C_i, so T_i equals the averaged
 // deferred term omega / |J_i| sum_k Mbar_ik of Eq. 5.
+// One thread per variable (no grid-stride loop: the block scheduler keeps
+// every warp slot busy).  Variables with at most two copies -- most of them --
+// fetch their slot positions from one 16-byte record, so their multipliers are
+// two dependent loads away; longer lists continue in csr_pos.
 __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
-        const int ii = find_inst(a.prefix, a.n_inst, g);
-        const InstDev* __restrict__ I = a.insts + ii;
-        if (I->ctl->done) continue;
-        const int i = g - __ldg(a.prefix + ii);
-        const int b = I->csr_off[i], e = I->csr_off[i + 1];
-        if (b == e) continue;
-        const float* __restrict__ lam = I->lam;
-        const int32_t* __restrict__ pos = I->csr_pos;
-        float s = 0.f;
-        for (int p = b; p < e; ++p) s += lam[pos[p]];
-        I->T[i] = (I->C[i] - s) / static_cast<float>(e - b);
-    }
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.total) return;
+    const int ii = find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    if (I->ctl->done) return;
+    const int i = g - __ldg(a.prefix + ii);
+    const int4 r = reinterpret_cast<const int4*>(I->vrec)[i];
+    if (r.w == 0) return;
+    const float ci = I->C[i];
+    const float* __restrict__ lam = I->lam;
+    const float l0 = lam[r.x];
+    const float l1 = r.w > 1 ? lam[r.y] : 0.f;
+    float s = 0.f + l0;  // ascending slot order, as in csr_pos: a fixed summation order
+    if (r.w > 1) s += l1;
+    for (int p = r.z + 2; p < r.z + r.w; ++p) s += lam[I->csr_pos[p]];
+    I->T[i] = (ci - s) / static_cast<float>(r.w);
 }
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
@@ -64,54 +71,70 @@ struct LbArgs {
     int32_t target;
 };
 
+// (s, c) <- (s, c) + (x, y) for Neumaier pairs
+__device__ __forceinline__ void neumaier_pair(double& s, double& c, double x, double y) {
+    neumaier(s, c, x);
+    c += y;
+}
+
+// block-wide fixed-order reduction of one Neumaier pair per thread (blockDim.x == 256)
+__device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double s, double c) {
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double x = ss[threadIdx.x], cc = sc[threadIdx.x];
+            neumaier_pair(x, cc, ss[threadIdx.x + w], sc[threadIdx.x + w]);
+            ss[threadIdx.x] = x;
+            sc[threadIdx.x] = cc;
+        }
+        __syncthreads();
+    }
+}
+
+// One block per chunk of kLbChunk tiles (one tile per thread), then the last
+// block of the instance sums the chunk partials.  The chunking depends only
+// on the instance, so its bound is the same alone or in a batch.
 __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     __shared__ double ss[256], sc[256];
+    __shared__ int last;
     const int g = blockIdx.x;
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     InstCtl* ctl = I->ctl;
     if (a.target == kLbIterate && ctl->done) return;
     const int c = g - __ldg(a.prefix + ii);
-    const int t0 = c * kLbChunk;
-    const int t1 = min(t0 + kLbChunk, I->n_tiles);
-    double s = 0.0, cp = 0.0;
-    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) neumaier(s, cp, I->tile_lb[t]);
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = cp;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            double x = ss[threadIdx.x], y = ss[threadIdx.x + w], cc = sc[threadIdx.x] + sc[threadIdx.x + w];
-            neumaier(x, cc, y);
-            ss[threadIdx.x] = x;
-            sc[threadIdx.x] = cc;
-        }
-        __syncthreads();
-    }
+    const int t = c * kLbChunk + threadIdx.x;
+    block_pair_reduce(ss, sc, t < I->n_tiles ? I->tile_lb[t] : 0.0, 0.0);
     if (threadIdx.x == 0) {
         I->chunk_lb[c] = ss[0] + sc[0];
         __threadfence();
-        const int ticket = atomicAdd(&ctl->ticket, 1);
-        if (ticket == I->n_chunks - 1) {
-            __threadfence();
-            double S = 0.0, Cc = 0.0;
-            for (int q = 0; q < I->n_chunks; ++q) neumaier(S, Cc, __ldcg(I->chunk_lb + q));
-            neumaier(S, Cc, I->const_lb);
-            const double lb = S + Cc;
-            ctl->ticket = 0;
-            if (a.target == kLbIterate) {
-                const int it = ctl->iter;
-                ctl->lb_ring[it % kLbRing] = lb;
-                ctl->lb_last = lb;
-                ctl->iter = it + 1;
-                const int since = ++ctl->since_reset;
-                if (ctl->stop_enabled && since >= ctl->min_iters && since > ctl->window) {
-                    const double prev = ctl->lb_ring[(it - ctl->window) % kLbRing];
-                    if (lb - prev <= ctl->tol * fmax(fabs(lb), 1.0)) ctl->done = 1;
-                }
-            } else {
-                ctl->lb_eval = lb;
+        last = atomicAdd(&ctl->ticket, 1) == I->n_chunks - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0, cp = 0.0;
+    for (int q = threadIdx.x; q < I->n_chunks; q += blockDim.x) neumaier(s, cp, __ldcg(I->chunk_lb + q));
+    block_pair_reduce(ss, sc, s, cp);
+    if (threadIdx.x == 0) {
+        double S = ss[0], Cc = sc[0];
+        neumaier(S, Cc, I->const_lb);
+        const double lb = S + Cc;
+        ctl->ticket = 0;
+        if (a.target == kLbIterate) {
+            const int it = ctl->iter;
+            ctl->lb_ring[it % kLbRing] = lb;
+            ctl->lb_last = lb;
+            ctl->iter = it + 1;
+            const int since = ++ctl->since_reset;
+            if (ctl->stop_enabled && since >= ctl->min_iters && since > ctl->window) {
+                const double prev = ctl->lb_ring[(it - ctl->window) % kLbRing];
+                if (lb - prev <= ctl->tol * fmax(fabs(lb), 1.0)) ctl->done = 1;
             }
+        } else {
+            ctl->lb_eval = lb;
         }
     }
 }
@@ -299,7 +322,10 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
         cudaError_t e;
-        switch (W) {
+        if (cls == kJitClass) {
+            void* kargs[] = {&args};
+            e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, 0, s);
+        } else switch (W) {
             case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
             case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
             case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
@@ -321,7 +347,7 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
     const bool timed = cfg.prof && cfg.prof->on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-    reduce_T_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
+    reduce_T_kernel<<<(b.vars_total + 255) / 256, 256, 0, s>>>(
         flat(b, b.var_prefix, b.vars_total));
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
     cfg.count();

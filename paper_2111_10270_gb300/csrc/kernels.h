@@ -25,7 +25,7 @@ constexpr int kMMBoth = 2;   // write m0 and m1 (else M = m1 - m0 into mm0)
 constexpr int kLbIterate = 0;  // running bound of an iteration: ring, counter, stopping rule
 constexpr int kLbEval = 1;     // evaluation: InstCtl::lb_eval
 
-constexpr int kLbChunk = 4096;   // tiles per block of the lower-bound reduction
+constexpr int kLbChunk = 256;    // tiles per block of the lower-bound reduction (one per thread)
 constexpr int kObjChunk = 8192;  // variables per block of the objective reduction
 
 // Device-side description of a batch of instances (one or many).  Work of
@@ -46,17 +46,9 @@ struct DevBatch {
     int32_t* objchunk_prefix = nullptr;      // [n_inst + 1]
     int32_t objchunks_total = 0;
     int32_t n_inst = 0;
+    JitKernels jit;                          // kernels of the shape-specialised class
 };
 
-struct SweepArgs {
-    const InstDev* insts;
-    const int32_t* prefix;  // [n_inst + 1] tiles of this class per instance
-    const int32_t* first;   // [n_inst] first tile of this class in the instance
-    int32_t n_inst;
-    int32_t total;
-    int32_t kstride;        // shared-memory kernels: per-layer stride (>= longest row)
-    int32_t flags;          // kMMAddT | kMMBoth
-};
 
 // CUDA-event timing of the update sweeps and the deferred-sum kernel
 struct Profiler {

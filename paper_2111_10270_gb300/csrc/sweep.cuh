@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 #pragma unroll
                 for (int v = 0; v < W; ++v) f[v] = nf[v];
             }
-            term = E - omega * negsum;
+            term = fmaf(-omega, negsum, E);
         }
 
         if constexpr (MODE == kBwdUpdate) {
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 #pragma unroll
                 for (int v = 0; v < W; ++v) b[v] = nb[v];
             }
-            term = b[0] - omega * negsum;
+            term = fmaf(-omega, negsum, b[0]);
         }
 
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {

@@ -16,8 +16,10 @@ def rel_err(a, b):
     return np.abs(a - b) / np.maximum(1.0, np.maximum(np.abs(a), np.abs(b)))
 
 
-def lb_close(a, b, rtol=LB_RTOL):
-    return abs(a - b) <= rtol * max(1.0, abs(a), abs(b))
+def lb_close(a, b, rtol=LB_RTOL, scale=0.0):
+    """|a - b| <= rtol * max(1, |a|, |b|, scale).  `scale` is the conditioning
+    of the bound as a sum, sum_j |E_j| (0 for the plain relative test)."""
+    return abs(a - b) <= rtol * max(1.0, abs(a), abs(b), scale)
 
 
 def slot_order(orc, gpu_var, gpu_row):

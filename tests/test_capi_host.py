@@ -155,6 +155,26 @@ def test_wide_and_long_rows_plan(P, oracle_mod):
     assert (info["n_bdds"], info["n_slots"], info["n_nodes"]) == (orc.m, orc.S, orc.N)
 
 
+def test_specialised_kernels_compile_on_the_host(P):
+    """The shape-specialised kernels are generated and compiled with NVRTC
+    while planning (no GPU needed): every narrow short shape gets one."""
+    g = ilpgen.mrf_grid(8, 8, 3, 0)
+    inst = P.Instance.from_ilp(g)
+    inst.plan()
+    kp = inst.kernel_plan()
+    assert kp["note"] == "" and kp["jit_shapes"] == 2 and kp["static_tiles"] == 0
+    off = P.Instance.from_ilp(g, jit=-1)
+    off.plan()
+    kp = off.kernel_plan()
+    assert kp["jit_shapes"] == 0 and kp["jit_tiles"] == 0 and kp["static_tiles"] > 0
+    # random rows of many shapes, including ones too wide or long for the specialised code
+    ilp = ilpgen.random_ilp(60, 50, 77, max_row=20, max_coef=2)
+    inst = P.Instance.from_ilp(ilp)
+    inst.plan()
+    kp = inst.kernel_plan()
+    assert kp["note"] == "" and kp["jit_shapes"] > 0
+
+
 def test_infeasible_instance_is_reported(P):
     rb = ilpgen._RowBuilder()
     rb.add([0, 1], [1, 1], 0, 2)

@@ -465,3 +465,13 @@ def test_uniform_draws_cover_the_interval(oracle_mod):
     assert r.min() >= -1.0 and r.max() < 1.0
     assert abs(r.mean()) < 0.03 and abs(r.std() - 1 / np.sqrt(3)) < 0.02
     assert len(np.unique(r)) == len(r)
+
+
+def test_energies_sum_to_the_running_bound(oracle_mod):
+    ilp = ilpgen.random_ilp(9, 7, 4242, max_row=5)
+    p = oracle_mod.Problem.from_ilp(ilp)
+    p.iterate(3)
+    run, _ = p.lower_bounds()
+    assert abs(p.energies().sum() + p.const_lb - run) < 1e-12
+    hi, lo, _, _ = p.state()
+    assert abs(p.energies().sum() + p.const_lb - lifted_energy_bruteforce(p, ilp, hi, lo)) < 1e-9

@@ -42,8 +42,8 @@ WORKLOADS = {
 }
 METRIC = "BDD arc-updates/s (full FastDOG solve: dual sweeps to the 1e-4 LB gap + perturbation rounding)"
 UNIT = "arc-updates/s"
-SWEEP_SRC = os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", "sweep.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+SWEEP_SRCS = [os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", f) for f in ("jit.cpp", "jit_skeleton.cuh")]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.txt")
 
 
 def parse():
@@ -187,13 +187,21 @@ def solve(inst, max_iters, kr, dual_only=False):
 
 
 def sweep_traffic():
+    """DRAM bytes per update-sweep launch from the committed ncu summary, if
+    the sweep's generator sources are unchanged since that capture."""
     try:
+        rec = {}
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)
-        sha = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()
-        if rec.get("sweep_source_sha256") == sha:
-            return rec.get("dram_bytes_per_launch")
-    except (OSError, ValueError):
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    rec[k.strip()] = v.strip()
+        h = hashlib.sha256()
+        for f in SWEEP_SRCS:
+            h.update(open(f, "rb").read())
+        if rec.get("sweep_source_sha256") == h.hexdigest():
+            return int(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
@@ -279,7 +287,8 @@ def main():
     if not peak:
         peak = 6800.0
     reduce_bytes = 8 * S + 12 * g.n_vars + 4  # per launch: slot index + gathered lambda; offsets, target, result
-    roofline = {"bound": "hbm", "kernel": "sweep_kernel<W=2,reg,update>", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "fdog_jit_fwd / fdog_jit_bwd (shape-specialised update sweeps)",
+                "achieved": achieved, "peak": peak,
                 "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak if achieved else None,
                 "traffic": sweep_traffic(), "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_us": sweep_avg_s * 1e6, "launches": prof["sweep_launches"],

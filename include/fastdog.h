@@ -272,6 +272,29 @@ int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* swee
                       double* reduce_ms, int64_t* kernel_launches);
 
 /*
+ * Allocation-free lower-bound reduction (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory -- plug-ins whose host
+ * framework owns every device allocation through its own pool, and real-time
+ * loops that forbid allocation after start-up).
+ * Writes to dev_out[0] the deterministic FP64 compensated sum
+ * constant + sum_{t < n} dev_values[t] -- e.g. per-subproblem energies E_j, so
+ * that the result is the bound sum_j E^j of Eq. D -- using the same fixed
+ * chunking as the library's own bound reduction.  dev_values (n doubles) and
+ * dev_out (one double) are device memory owned by the caller; the call
+ * allocates nothing: its scratch is a static device array of 256 KiB that
+ * every GPU loading this library holds until the process exits.
+ * n may be at most 8,388,608 (FDOG_EINVAL beyond, or for negative n or NULL
+ * pointers).  The first call on a device looks up that array's device address
+ * with the device current; make that first call before any stream capture.
+ * Work is queued on cuda_stream (NULL: legacy default stream); the call does
+ * not wait for it.  All calls share the one scratch array, so calls whose
+ * kernels overlap on the GPU (different streams, or several host threads)
+ * race: serialise them.  Errors: FDOG_EINVAL, FDOG_ECUDA.
+ */
+int fdog_bound_reduce_noalloc(const double* dev_values, int64_t n, double constant, double* dev_out,
+                              void* cuda_stream);
+
+/*
  * Human-readable detail of the last error status returned for this instance
  * (empty if none).  The pointer stays valid until the next call on inst.
  */

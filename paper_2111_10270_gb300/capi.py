@@ -79,6 +79,7 @@ SIGNATURES = {
     "fdog_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "fdog_info": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "fdog_bound_reduce_noalloc": (ctypes.c_int, [_P, _i64, _f64, _P, _P]),
     "fdog_last_error": (ctypes.c_char_p, [_P]),
     "fdog_destroy": (None, [_P]),
     "fdog_status_string": (ctypes.c_char_p, [ctypes.c_int]),

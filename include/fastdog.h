@@ -78,6 +78,10 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *                              build time with NVRTC for rows of width <= 4 and
  *                              length <= 16: 0 = use them when available
  *                              (falls back to the generic kernels), -1 = never
+ *   fuse = 0                   deferred sums of variables whose copies all lie
+ *                              in one tile of 32 BDDs are formed inside the
+ *                              update sweep (same operations, same order);
+ *                              -1 = leave every variable to the separate pass
  */
 typedef struct {
     double omega;
@@ -91,7 +95,8 @@ typedef struct {
     uint64_t seed;
     int32_t block_threads;
     int32_t jit;
-    int32_t reserved[6];
+    int32_t fuse;
+    int32_t reserved[5];
 } fdog_params;
 
 /* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */
@@ -135,12 +140,14 @@ int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed);
 /*
  * Which sweep kernels a planned instance uses: *jit_shapes distinct shapes
  * with shape-specialised kernels, covering *jit_tiles tiles of 32 BDDs;
- * *static_tiles tiles run the generic kernels.  If the specialised kernels
- * could not be compiled, `note` (capacity note_cap, may be NULL) receives the
- * reason.  Any pointer may be NULL.  FDOG_ESTATE if not planned.
+ * *static_tiles tiles run the generic kernels; *local_vars variables have all
+ * their copies in one tile, so the update sweep forms their deferred terms
+ * (params.fuse).  If the specialised kernels could not be compiled, `note`
+ * (capacity note_cap, may be NULL) receives the reason.  Any pointer may be
+ * NULL.  FDOG_ESTATE if not planned.
  */
 int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
-                     char* note, int32_t note_cap);
+                     int64_t* local_vars, char* note, int32_t note_cap);
 int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes, int32_t* vars, int32_t* lstart,
                  int32_t* lo, int32_t* hi);
 

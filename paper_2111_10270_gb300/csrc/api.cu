@@ -74,7 +74,10 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.cost), sizeof(double) * sz(n)},
         {reinterpret_cast<void**>(&a.csr_off), sizeof(int32_t) * static_cast<size_t>(n + 1)},
         {reinterpret_cast<void**>(&a.csr_pos), sizeof(int32_t) * sz(d.n_slots)},
-        {reinterpret_cast<void**>(&a.vrec), 4 * sizeof(int32_t) * sz(n)},
+        {reinterpret_cast<void**>(&a.vrec), 2 * sizeof(int32_t) * sz(n)},
+        {reinterpret_cast<void**>(&a.patterns), sizeof(int32_t) * std::max<size_t>(d.patterns.size(), 2)},
+        {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * std::max<size_t>(d.local_ent.size(), 4)},
+        {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * std::max<size_t>(d.work.size(), 1)},
         {reinterpret_cast<void**>(&a.tile_lb), sizeof(double) * sz(nt)},
         {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
         {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
@@ -102,7 +105,8 @@ int plan(fdog_instance* inst) {
     try {
         rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
                                  inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(),
-                                 inst->params.jit >= 0 && !inst->jit_failed, inst->dec, inst->last_error);
+                                 inst->params.jit >= 0 && !inst->jit_failed, inst->params.fuse >= 0, inst->dec,
+                                 inst->last_error);
     } catch (const std::bad_alloc&) {
         rc = FDOG_ENOMEM;
     } catch (...) {
@@ -168,6 +172,10 @@ int allocate_and_upload(fdog_instance* inst) {
     h.csr_off = a.csr_off;
     h.csr_pos = a.csr_pos;
     h.vrec = a.vrec;
+    h.patterns = a.patterns;
+    h.local_ent = a.local_ent;
+    h.work = a.work;
+    h.n_work = static_cast<int32_t>(d.work.size());
     h.cost = a.cost;
     h.pert = a.pert;
     h.x = a.x;
@@ -209,6 +217,9 @@ int allocate_and_upload(fdog_instance* inst) {
     };
     two(&b.var_prefix, static_cast<int32_t>(n));
     b.vars_total = static_cast<int32_t>(n);
+    two(&b.work_prefix, static_cast<int32_t>(d.work.size()));
+    b.work_total = static_cast<int32_t>(d.work.size());
+    for (int c = 0; c < kNumClasses; ++c) b.has_local[c] = d.cls_has_local[c];
     two(&b.slot_prefix, static_cast<int32_t>(S));
     b.slots_total = static_cast<int32_t>(S);
     two(&b.chunk_prefix, static_cast<int32_t>(nt > 0 ? nchunks : 0));
@@ -229,6 +240,9 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
     up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
     up(a.vrec, d.vrec.data(), sizeof(int32_t) * d.vrec.size());
+    up(a.patterns, d.patterns.data(), sizeof(int32_t) * d.patterns.size());
+    up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
+    up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());
     up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
     if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
     return FDOG_OK;
@@ -447,10 +461,11 @@ int fdog_plan(fdog_instance* inst, int64_t* device_bytes) {
 }
 
 int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
-                     char* note, int32_t note_cap) {
+                     int64_t* local_vars, char* note, int32_t note_cap) {
     if (!inst) return FDOG_EINVAL;
     if (!inst->planned) return FDOG_ESTATE;
     const Decomposition& d = inst->dec;
+    if (local_vars) *local_vars = d.n_local_vars;
     if (jit_shapes) *jit_shapes = static_cast<int32_t>(jit_ids(inst).size());
     const int64_t jt = d.cls_tile_begin[kJitClass + 1] - d.cls_tile_begin[kJitClass];
     if (jit_tiles) *jit_tiles = jt;

@@ -162,7 +162,7 @@ std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) 
 
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        bool use_jit, Decomposition& out, std::string& err) {
+                        bool use_jit, bool fuse_local, Decomposition& out, std::string& err) {
     out = Decomposition();
     out.fixed.assign(n_vars, -1);
 
@@ -308,7 +308,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     for (size_t q = 0; q < bdds.size();) {
         size_t e = q;
         while (e < bdds.size() && e - q < static_cast<size_t>(kTile) && bdds[e].shape == bdds[q].shape) ++e;
-        TileDev t{bdds[q].shape, static_cast<int32_t>(slot), static_cast<int32_t>(e - q), static_cast<int32_t>(q)};
+        TileDev t{bdds[q].shape, static_cast<int32_t>(slot), static_cast<int32_t>(e - q), static_cast<int32_t>(q), -1,
+                  {0, 0, 0}};
         int k = out.shapes[bdds[q].shape].k;
         slot += static_cast<int64_t>(k) * kTile;
         if (slot > INT32_MAX) { err = "more than 2^31 padded slots"; return FDOG_EUNSUPPORTED; }
@@ -350,15 +351,59 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
     for (int64_t p = 0; p < slot; ++p)
         if (out.var[p] >= 0) out.csr_pos[fill[out.var[p]]++] = static_cast<int32_t>(p);
-    // per-variable records: the first two slots inline, so that most variables
-    // need one record load before their multipliers can be fetched
-    out.vrec.resize(4 * static_cast<size_t>(n_vars));
+    // per-variable 8-byte records: variables with one or two copies (most of
+    // them) carry their slots inline, so their multipliers are one dependent
+    // load away; longer lists are referenced into csr_pos
+    out.vrec.resize(2 * static_cast<size_t>(n_vars));
     for (int32_t i = 0; i < n_vars; ++i) {
         const int32_t b = out.csr_off[i], c = out.csr_off[i + 1] - b;
-        out.vrec[4 * i + 0] = c > 0 ? out.csr_pos[b] : -1;
-        out.vrec[4 * i + 1] = c > 1 ? out.csr_pos[b + 1] : -1;
-        out.vrec[4 * i + 2] = b;
-        out.vrec[4 * i + 3] = c;
+        if (c == 1 || c == 2) {
+            out.vrec[2 * i] = out.csr_pos[b];
+            out.vrec[2 * i + 1] = c == 2 ? out.csr_pos[b + 1] : -1;
+        } else {
+            out.vrec[2 * i] = -(b + 1);
+            out.vrec[2 * i + 1] = c;
+        }
+    }
+    // Tile-local variables: every copy in one tile (at most four copies).  The
+    // update sweep computes their deferred term itself; the deferred-sum
+    // kernel keeps the rest.  Tiles with equal local-variable patterns share
+    // one pattern.
+    std::vector<uint8_t> local(n_vars, 0);
+    if (fuse_local) {
+        std::unordered_map<std::string, int> pat_ids;
+        std::vector<uint16_t> ent;
+        for (size_t ti = 0; ti < out.tiles.size(); ++ti) {
+            TileDev& t = out.tiles[ti];
+            const int64_t lo = t.slot_base, hi = lo + static_cast<int64_t>(out.shapes[t.shape].k) * kTile;
+            ent.clear();
+            for (int64_t p = lo; p < hi; ++p) {
+                const int32_t v = out.var[p];
+                if (v < 0) continue;
+                const int32_t b = out.csr_off[v], c = out.csr_off[v + 1] - b;
+                if (c > 4 || out.csr_pos[b] != p || out.csr_pos[b + c - 1] >= hi) continue;  // p is the first copy
+                for (int q = 0; q < 4; ++q)
+                    ent.push_back(q < c ? static_cast<uint16_t>(out.csr_pos[b + q] - lo) : uint16_t(0xFFFF));
+                local[v] = 1;
+            }
+            if (ent.empty()) continue;
+            std::string key(reinterpret_cast<const char*>(ent.data()), ent.size() * sizeof(uint16_t));
+            auto it = pat_ids.find(key);
+            if (it == pat_ids.end()) {
+                it = pat_ids.emplace(std::move(key), static_cast<int>(out.patterns.size() / 2)).first;
+                out.patterns.push_back(static_cast<int32_t>(out.local_ent.size() / 4));
+                out.patterns.push_back(static_cast<int32_t>(ent.size() / 4));
+                out.local_ent.insert(out.local_ent.end(), ent.begin(), ent.end());
+            }
+            t.pattern = it->second;
+            for (int c = 0; c < kNumClasses; ++c)
+                if (static_cast<int32_t>(ti) >= out.cls_tile_begin[c] && static_cast<int32_t>(ti) < out.cls_tile_begin[c + 1])
+                    out.cls_has_local[c] = true;
+        }
+    }
+    for (int32_t i = 0; i < n_vars; ++i) {
+        if (local[i]) ++out.n_local_vars;
+        else if (out.csr_off[i + 1] > out.csr_off[i]) out.work.push_back(i);
     }
     return FDOG_OK;
 }

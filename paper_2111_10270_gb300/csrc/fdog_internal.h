@@ -57,6 +57,8 @@ struct TileDev {
     int32_t slot_base;
     int32_t n_valid;   // BDDs in this tile (1..kTile)
     int32_t bdd_base;  // index of lane 0's BDD in the instance's BDD order
+    int32_t pattern;   // tile-local variables: index into InstDev::patterns, -1 if none
+    int32_t pad[3];
 };
 
 #define FDOG_LB_RING 64
@@ -93,7 +95,11 @@ struct InstDev {
     float* C;                // [n] target sum_j lambda^j_i (= c_i, perturbed by rounding)
     const int32_t* csr_off;  // [n + 1]
     const int32_t* csr_pos;  // [slots] padded slot positions of each variable, ascending
-    const int32_t* vrec;     // [4 n] {first slot, second slot or -1, csr_off, |J_i|}, 16-byte aligned
+    const int32_t* vrec;     // [2 n] per variable {a, b}: a >= 0: copies at slots a and b (b = -1: one copy);
+                             //       a < 0: |J_i| = b copies listed at csr_pos[-a - 1 ...]
+    const int32_t* patterns; // [2 per pattern] {first entry, entries}: variables whose copies all lie in one tile
+    const uint16_t* local_ent;  // [4 per entry] copy offsets (32 t + lane) within the tile, ascending, 0xFFFF unused
+    const int32_t* work;     // [n_work] variables the deferred-sum kernel handles (copies in several tiles)
     const double* cost;      // [n]
     float* pert;             // [n] rounding perturbation of this round
     uint8_t* x;              // [n] rounded solution
@@ -105,8 +111,8 @@ struct InstDev {
     int32_t n_vars;
     int32_t n_chunks;
     int32_t n_obj_chunks;
+    int32_t n_work;
     float omega;
-    float pad0;
     double const_lb;
 };
 
@@ -118,6 +124,8 @@ struct SweepArgs {
     int32_t total;
     int32_t kstride;        // shared-memory kernels: per-layer stride (>= longest row)
     int32_t flags;          // evaluate at lambda + T (1) | write m0 and m1 (2)
+    int32_t epi;            // update passes: layer stride of the per-warp staging for tile-local
+                            // deferred sums (0: no tile of this launch has local variables)
 };
 
 // </jit-abi>
@@ -152,7 +160,12 @@ struct Decomposition {
     std::vector<int32_t> cls_tile_begin;  // kNumClasses + 1 (tiles sorted by class)
     std::vector<int32_t> var;      // padded slots
     std::vector<int32_t> csr_off, csr_pos;
-    std::vector<int32_t> vrec;     // 4 ints per variable: {first slot, second slot or -1, csr_off, count}
+    std::vector<int32_t> vrec;     // 2 ints per variable (see InstDev::vrec)
+    std::vector<int32_t> patterns;  // 2 ints per pattern (see InstDev::patterns)
+    std::vector<uint16_t> local_ent;
+    std::vector<int32_t> work;      // variables left to the deferred-sum kernel
+    int64_t n_local_vars = 0;
+    bool cls_has_local[kNumClasses] = {false};
     std::vector<ShapeDev> shape_dev;
     std::vector<uint16_t> tpl;
     int64_t n_bdds = 0, n_slots = 0, n_nodes = 0, slots_pad = 0;
@@ -164,7 +177,7 @@ struct Decomposition {
 // Returns an FDOG_* status.
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        bool use_jit, Decomposition& out, std::string& err);
+                        bool use_jit, bool fuse_local, Decomposition& out, std::string& err);
 
 // shape-specialised code (jit.cpp): process-wide shape registry and kernels
 int jit_register_shape(const HostShape& s);  // id of the shape's structure

@@ -12,7 +12,7 @@
 namespace fdog {
 
 // prefix ints of a one-instance batch: per class 3 (prefix[2], first[1]) + 4 x 2
-constexpr int kPrefixInts = 3 * kNumClasses + 8;
+constexpr int kPrefixInts = 3 * kNumClasses + 10;
 
 struct DevArrays {
     InstDev* inst = nullptr;
@@ -32,6 +32,9 @@ struct DevArrays {
     int32_t* csr_off = nullptr;
     int32_t* csr_pos = nullptr;
     int32_t* vrec = nullptr;
+    int32_t* patterns = nullptr;
+    uint16_t* local_ent = nullptr;
+    int32_t* work = nullptr;
     double* tile_lb = nullptr;
     double* chunk_lb = nullptr;
     double* obj_chunk = nullptr;

@@ -108,15 +108,20 @@ void emit_shape(std::ostringstream& o, const HostShape& s, int id, int mode) {
         return x >= 0 ? x - s.lstart[t + 1] : x;
     };
     o << "__device__ __forceinline__ float shp_" << id << "_" << mode
-      << "(const InstDev* __restrict__ I, long long base, bool valid, int flags) {\n";
+      << "(const InstDev* __restrict__ I, long long base, bool valid, int flags, bool local, float* ep_lam, "
+         "int* ep_var) {\n";
+    o << "  (void)local; (void)ep_lam; (void)ep_var;\n";
     o << "  float* __restrict__ lam = I->lam;\n  const float omega = I->omega;\n  (void)omega; (void)flags;\n";
     for (int t = 0; t < k; ++t) o << "  float " << nm("l", t) << " = 0.f, " << nm("u", t) << " = 0.f;\n";
     o << "  if (valid) {\n";
     for (int t = 0; t < k; ++t) o << "    " << nm("l", t) << " = lam[base + " << 32 * t << "];\n";
     const char* need_u = mode <= 1 ? "true" : "(flags & 1)";
     o << "    if (" << need_u << ") {\n";
-    for (int t = 0; t < k; ++t)
-        o << "      " << nm("u", t) << " = I->T[I->var[base + " << 32 * t << "]];\n";
+    for (int t = 0; t < k; ++t) {
+        o << "      { const int v = I->var[base + " << 32 * t << "]; " << nm("u", t) << " = I->T[v];";
+        if (mode <= 1) o << " if (local) ep_var[" << 32 * t << "] = v;";
+        o << " }\n";
+    }
     if (mode >= 2)
         for (int t = 0; t < k; ++t) o << "      " << nm("l", t) << " += " << nm("u", t) << ";\n";
     o << "    }\n  }\n";
@@ -213,6 +218,8 @@ void emit_shape(std::ostringstream& o, const HostShape& s, int id, int mode) {
     if (mode <= 1) {
         o << "  if (valid) {\n";
         for (int t = 0; t < k; ++t) o << "    lam[base + " << 32 * t << "] = " << nm("l", t) << ";\n";
+        o << "  }\n  if (local) {\n";
+        for (int t = 0; t < k; ++t) o << "    ep_lam[" << 32 * t << "] = " << nm("l", t) << ";\n";
         o << "  }\n";
     }
     o << "  return term;\n}\n\n";
@@ -230,7 +237,8 @@ std::string generate_module(const std::vector<int>& ids) {
     for (int mode = 0; mode < 4; ++mode) {
         o << "  " << (mode ? "else " : "") << "if (MODE == " << mode << ") { switch (jit) { \\\n";
         for (int id : ids)
-            o << "    case " << id << ": term = shp_" << id << "_" << mode << "(I, (long long)base, valid, a.flags); break; \\\n";
+            o << "    case " << id << ": term = shp_" << id << "_" << mode
+              << "(I, base, valid, a.flags, local, ep_lam + lane, ep_var + lane); break; \\\n";
         o << "    default: break; } } \\\n";
     }
     o << "\n" << kJitSkeleton;

@@ -21,13 +21,34 @@ __device__ __forceinline__ int fdog_find_inst(const int32_t* __restrict__ prefix
     return lo;
 }
 
+// Deferred terms of the tile-local variables, formed right after an update
+// pass from the staged multipliers (same sum and order as the deferred-sum
+// kernel); staging: layer t lane l at [32 t + l].
+__device__ __forceinline__ void fdog_tile_local_sums(const InstDev* __restrict__ I, int pattern,
+                                                     const float* ep_lam, const int* ep_var, int lane) {
+    const int2 pat = reinterpret_cast<const int2*>(I->patterns)[pattern];
+    for (int e = lane; e < pat.y; e += 32) {
+        const ushort4 o = reinterpret_cast<const ushort4*>(I->local_ent)[pat.x + e];
+        float s = 0.f + ep_lam[o.x];
+        int c = 1;
+        if (o.y != 0xFFFFu) { s += ep_lam[o.y]; ++c; }
+        if (o.z != 0xFFFFu) { s += ep_lam[o.z]; ++c; }
+        if (o.w != 0xFFFFu) { s += ep_lam[o.w]; ++c; }
+        const int v = ep_var[o.x];
+        I->T[v] = (I->C[v] - s) / (float)c;
+    }
+}
+
 // MODE: 0 ascending pass with updates, 1 descending pass with updates,
 //       2 min-marginals, 3 energies only
 template <int MODE>
 __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
+    extern __shared__ float fdog_smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
+    float* ep_lam = fdog_smem + (long long)wib * a.epi * 32 * 2;
+    int* ep_var = (int*)(ep_lam + (long long)a.epi * 32);
     for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
         const int ii = fdog_find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
@@ -36,9 +57,15 @@ __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
         const TileDev tile = I->tiles[ti];
         const int jit = I->shapes[tile.shape].jit;
         const bool valid = lane < tile.n_valid;
-        const size_t base = (size_t)tile.slot_base + lane;
+        const long long base = (long long)tile.slot_base + lane;
+        const bool local = MODE <= 1 && a.epi > 0 && tile.pattern >= 0;
         float term = 0.f;
         FDOG_DISPATCH(MODE)
+        if (local) {
+            __syncwarp();
+            fdog_tile_local_sums(I, tile.pattern, ep_lam, ep_var, lane);
+            __syncwarp();
+        }
         float s = valid ? term : 0.f, comp = 0.f;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {

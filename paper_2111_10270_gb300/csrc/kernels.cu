@@ -36,26 +36,33 @@ struct FlatArgs {
 // sum_j lambda^j_i + omega sum_j M_ij = C_i, so T_i equals the averaged
 // deferred term omega / |J_i| sum_k Mbar_ik of Eq. 5.
 // One thread per variable (no grid-stride loop: the block scheduler keeps
-// every warp slot busy).  Variables with at most two copies -- most of them --
-// fetch their slot positions from one 16-byte record, so their multipliers are
-// two dependent loads away; longer lists continue in csr_pos.
+// every warp slot busy).  Variables with one or two copies -- most of them --
+// read their slot positions from an 8-byte record, so their multipliers are
+// one dependent load away; longer lists continue in csr_pos.
 __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= a.total) return;
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     if (I->ctl->done) return;
-    const int i = g - __ldg(a.prefix + ii);
-    const int4 r = reinterpret_cast<const int4*>(I->vrec)[i];
-    if (r.w == 0) return;
-    const float ci = I->C[i];
+    const int i = I->work[g - __ldg(a.prefix + ii)];  // variables with copies in several tiles
+    const int2 r = reinterpret_cast<const int2*>(I->vrec)[i];
     const float* __restrict__ lam = I->lam;
-    const float l0 = lam[r.x];
-    const float l1 = r.w > 1 ? lam[r.y] : 0.f;
-    float s = 0.f + l0;  // ascending slot order, as in csr_pos: a fixed summation order
-    if (r.w > 1) s += l1;
-    for (int p = r.z + 2; p < r.z + r.w; ++p) s += lam[I->csr_pos[p]];
-    I->T[i] = (ci - s) / static_cast<float>(r.w);
+    float s = 0.f;
+    int cnt;
+    if (r.x >= 0) {
+        const float l0 = lam[r.x];
+        const float l1 = r.y >= 0 ? lam[r.y] : 0.f;
+        s += l0;  // ascending slot order, as in csr_pos: a fixed summation order
+        if (r.y >= 0) s += l1;
+        cnt = r.y >= 0 ? 2 : 1;
+    } else {
+        cnt = r.y;
+        if (cnt == 0) return;
+        const int32_t* __restrict__ pos = I->csr_pos + (-r.x - 1);
+        for (int p = 0; p < cnt; ++p) s += lam[pos[p]];
+    }
+    I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
 }
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
@@ -77,19 +84,30 @@ __device__ __forceinline__ void neumaier_pair(double& s, double& c, double x, do
     c += y;
 }
 
-// block-wide fixed-order reduction of one Neumaier pair per thread (blockDim.x == 256)
-__device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double s, double c) {
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
+// block-wide fixed-order reduction of one Neumaier pair per thread
+// (blockDim.x == 256): butterfly within each warp, then warp 0 combines the
+// eight warp results.  Every thread of warp 0 ends with the block total.
+__device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double& s, double& c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double os = __shfl_xor_sync(0xffffffffu, s, off);
+        const double oc = __shfl_xor_sync(0xffffffffu, c, off);
+        neumaier_pair(s, c, os, oc);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sc[threadIdx.x >> 5] = c;
+    }
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            double x = ss[threadIdx.x], cc = sc[threadIdx.x];
-            neumaier_pair(x, cc, ss[threadIdx.x + w], sc[threadIdx.x + w]);
-            ss[threadIdx.x] = x;
-            sc[threadIdx.x] = cc;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < 8 ? ss[threadIdx.x] : 0.0;
+        c = threadIdx.x < 8 ? sc[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+            const double os = __shfl_xor_sync(0xffffffffu, s, off);
+            const double oc = __shfl_xor_sync(0xffffffffu, c, off);
+            neumaier_pair(s, c, os, oc);
         }
-        __syncthreads();
     }
 }
 
@@ -97,7 +115,7 @@ __device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double
 // block of the instance sums the chunk partials.  The chunking depends only
 // on the instance, so its bound is the same alone or in a batch.
 __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
-    __shared__ double ss[256], sc[256];
+    __shared__ double ss[8], sc[8];
     __shared__ int last;
     const int g = blockIdx.x;
     const int ii = find_inst(a.prefix, a.n_inst, g);
@@ -106,20 +124,23 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     if (a.target == kLbIterate && ctl->done) return;
     const int c = g - __ldg(a.prefix + ii);
     const int t = c * kLbChunk + threadIdx.x;
-    block_pair_reduce(ss, sc, t < I->n_tiles ? I->tile_lb[t] : 0.0, 0.0);
+    double s = t < I->n_tiles ? I->tile_lb[t] : 0.0, cp = 0.0;
+    block_pair_reduce(ss, sc, s, cp);
     if (threadIdx.x == 0) {
-        I->chunk_lb[c] = ss[0] + sc[0];
+        I->chunk_lb[c] = s + cp;
         __threadfence();
         last = atomicAdd(&ctl->ticket, 1) == I->n_chunks - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double s = 0.0, cp = 0.0;
+    s = 0.0;
+    cp = 0.0;
     for (int q = threadIdx.x; q < I->n_chunks; q += blockDim.x) neumaier(s, cp, __ldcg(I->chunk_lb + q));
+    __syncthreads();  // the shared partials of the first reduction are reused
     block_pair_reduce(ss, sc, s, cp);
     if (threadIdx.x == 0) {
-        double S = ss[0], Cc = sc[0];
+        double S = s, Cc = cp;
         neumaier(S, Cc, I->const_lb);
         const double lb = S + Cc;
         ctl->ticket = 0;
@@ -308,15 +329,13 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
         const bool reg = class_is_reg(cls);
         const int W = class_width(cls);
         int wpb = cfg.warps_per_block;
-        size_t smem = 0;
-        int kstride = 0;
-        if (!reg) {
-            kstride = b.kmax[cls];
-            const size_t per_warp = static_cast<size_t>(kstride) * kTile * (2 + W) * sizeof(float);
-            while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
-            smem = per_warp * wpb;
-        }
-        SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags};
+        const int kstride = reg ? 0 : b.kmax[cls];
+        const int epi = ((mode == kFwdUpdate || mode == kBwdUpdate) && b.has_local[cls]) ? b.kmax[cls] : 0;
+        const size_t per_warp = (static_cast<size_t>(kstride) * (2 + W) + static_cast<size_t>(epi) * 2) * kTile *
+                                sizeof(float);
+        while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
+        const size_t smem = per_warp * wpb;
+        SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags, epi};
         const int blocks = blocks_for(total, wpb, cfg.num_sms * (2048 / (32 * wpb)));
         const bool timed = cfg.prof && cfg.prof->on && (mode == kFwdUpdate || mode == kBwdUpdate);
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -324,7 +343,11 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
         cudaError_t e;
         if (cls == kJitClass) {
             void* kargs[] = {&args};
-            e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, 0, s);
+            e = cudaSuccess;
+            if (smem > 48 * 1024)
+                e = cudaFuncSetAttribute(b.jit.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+            if (e == cudaSuccess) e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, smem, s);
         } else switch (W) {
             case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
             case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
@@ -343,12 +366,11 @@ static FlatArgs flat(const DevBatch& b, const int32_t* prefix, int total) {
 }
 
 cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
-    if (b.vars_total == 0) return cudaSuccess;
+    if (b.work_total == 0) return cudaSuccess;
     const bool timed = cfg.prof && cfg.prof->on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-    reduce_T_kernel<<<(b.vars_total + 255) / 256, 256, 0, s>>>(
-        flat(b, b.var_prefix, b.vars_total));
+    reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
     cfg.count();
     return cudaGetLastError();

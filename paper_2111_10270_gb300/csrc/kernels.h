@@ -39,6 +39,9 @@ struct DevBatch {
     int32_t kmax[kNumClasses] = {};
     int32_t* var_prefix = nullptr;           // [n_inst + 1]
     int32_t vars_total = 0;
+    int32_t* work_prefix = nullptr;          // [n_inst + 1] variables left to the deferred-sum kernel
+    int32_t work_total = 0;
+    bool has_local[kNumClasses] = {};        // some tile of the class has tile-local variables
     int32_t* slot_prefix = nullptr;          // [n_inst + 1] padded slots
     int32_t slots_total = 0;
     int32_t* chunk_prefix = nullptr;         // [n_inst + 1] lower-bound chunks

@@ -89,6 +89,25 @@ struct Store<W, false> {
 };
 
 
+// Deferred terms of the tile-local variables (every copy in this tile),
+// formed right after the pass from the staged multipliers: the same sum, in
+// the same ascending slot order, as the deferred-sum kernel uses.
+// ep_lam / ep_var: this warp's staging, layer t lane l at [32 t + l].
+__device__ __forceinline__ void tile_local_sums(const InstDev* __restrict__ I, int pattern, const float* ep_lam,
+                                                const int* ep_var, int lane) {
+    const int2 pat = reinterpret_cast<const int2*>(I->patterns)[pattern];
+    for (int e = lane; e < pat.y; e += 32) {
+        const ushort4 o = reinterpret_cast<const ushort4*>(I->local_ent)[pat.x + e];
+        float s = 0.f + ep_lam[o.x];
+        int c = 1;
+        if (o.y != 0xFFFFu) { s += ep_lam[o.y]; ++c; }
+        if (o.z != 0xFFFFu) { s += ep_lam[o.z]; ++c; }
+        if (o.w != 0xFFFFu) { s += ep_lam[o.w]; ++c; }
+        const int v = ep_var[o.x];
+        I->T[v] = (I->C[v] - s) / static_cast<float>(c);
+    }
+}
+
 // Loops over layers.  With REG the trip count is the constant kRegK and the
 // loops unroll completely, so every index into Store is a compile-time
 // constant and the arrays stay in registers.
@@ -120,10 +139,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
         const bool need_t = (MODE == kFwdUpdate || MODE == kBwdUpdate) || (a.flags & kMMAddT);
 
         Store<W, REG> S;
+        // per-warp shared memory: [Store arrays (shared-memory variants)] [staging for tile-local sums]
+        const size_t warp_floats =
+            (REG ? 0 : static_cast<size_t>(a.kstride) * kTile * (2 + W)) + static_cast<size_t>(a.epi) * kTile * 2;
+        float* wsm = smem + static_cast<size_t>(wib) * warp_floats;
         if constexpr (!REG) {
-            S.base = smem + static_cast<size_t>(wib) * a.kstride * kTile * (2 + W) + lane;
+            S.base = wsm + lane;
             S.stride = a.kstride;
         }
+        float* ep_lam = wsm + (REG ? 0 : static_cast<size_t>(a.kstride) * kTile * (2 + W));
+        int* ep_var = reinterpret_cast<int*>(ep_lam + static_cast<size_t>(a.epi) * kTile);
+        const bool local = (MODE == kFwdUpdate || MODE == kBwdUpdate) && a.epi > 0 && tile.pattern >= 0;
 
         // multipliers and deferred terms of every layer (coalesced per layer)
         FD_UP(t) {
@@ -131,7 +157,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             float l = 0.f, tb = 0.f;
             if (valid) {
                 l = lam[base + static_cast<size_t>(t) * kTile];
-                if (need_t) tb = I->T[I->var[base + static_cast<size_t>(t) * kTile]];
+                if (need_t) {
+                    const int v = I->var[base + static_cast<size_t>(t) * kTile];
+                    tb = I->T[v];
+                    if (local) ep_var[t * kTile + lane] = v;
+                }
             }
             if constexpr (MODE == kMinMarg || MODE == kEval) {
                 if (a.flags & kMMAddT) l += tb;
@@ -268,6 +298,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             FD_UP(t) {
                 if (t >= k) break;
                 if (valid) lam[base + static_cast<size_t>(t) * kTile] = S.L(t);
+                if (local) ep_lam[t * kTile + lane] = S.L(t);
+            }
+            if (local) {
+                __syncwarp();
+                tile_local_sums(I, tile.pattern, ep_lam, ep_var, lane);
+                __syncwarp();
             }
         }
 

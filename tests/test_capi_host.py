@@ -163,6 +163,8 @@ def test_specialised_kernels_compile_on_the_host(P):
     inst.plan()
     kp = inst.kernel_plan()
     assert kp["note"] == "" and kp["jit_shapes"] == 2 and kp["static_tiles"] == 0
+    # the 8 marginalisation rows of an edge share its 9 pairwise variables; 4 edges per tile
+    assert kp["local_vars"] > 0
     off = P.Instance.from_ilp(g, jit=-1)
     off.plan()
     kp = off.kernel_plan()

@@ -284,6 +284,27 @@ def test_specialised_and_generic_kernels_agree(P, seed):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
 
 
+@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+def test_tile_local_sums_match_the_separate_pass(P, jit):
+    """Deferred terms formed inside the sweep for tile-local variables use the
+    same operations in the same order as the deferred-sum kernel: the whole
+    state stays bitwise equal with the fusion on and off."""
+    g = ilpgen.mrf_grid(24, 20, 3, 51)
+    out = []
+    for fuse in (0, -1):
+        inst = P.Instance.from_ilp(g, tol=0.0, jit=jit, fuse=fuse)
+        inst.plan()
+        kp = inst.kernel_plan()
+        assert (kp["local_vars"] > 0) == (fuse == 0), kp
+        inst.build(0)
+        lbs = [inst.iterate(1)[1] for _ in range(20)]
+        _, _, lam = inst.multipliers()
+        rc, rounds = inst.primal_round()
+        x, obj, feas = inst.solution()
+        out.append((lbs, lam.tobytes(), rounds, x.tobytes(), obj))
+    assert out[0] == out[1]
+
+
 def test_runs_are_bitwise_deterministic(P):
     g = ilpgen.mrf_grid(16, 16, 4, 3)
     outs = []

@@ -275,10 +275,16 @@ def main():
     value = arcs / elapsed
 
     # ---- roofline of the dominant kernel (update sweep) ----------------------
+    kp = inst.kernel_plan()
     S = info["n_slots"]
     n_bdds = info["n_bdds"]
-    tiles = -(-n_bdds // 32)
-    alg_bytes = 16 * S + 24 * tiles  # per sweep launch: lambda r+w, var, deferred term gather; tile header + bound
+    tiles = kp["jit_tiles"] + kp["static_tiles"]
+    # per sweep launch: per slot lambda read + write, variable id, deferred-term gather (16 B); per tile its
+    # descriptor and bound partial (40 B); per tile-local variable its target C and new deferred term (8 B)
+    alg_bytes = 16 * S + 40 * tiles + 8 * kp["local_vars"]
+    # per deferred-sum launch: per listed variable its id, record, C and T (20 B); per copy the gathered
+    # multiplier (4 B), plus the overflow list entries of variables with more than two copies
+    reduce_bytes = 20 * kp["work_vars"] + 4 * kp["work_slots"] + 4 * max(kp["work_slots"] - 2 * kp["work_vars"], 0)
     sweep_avg_s = prof["sweep_ms"] / max(prof["sweep_launches"], 1) / 1e3
     reduce_avg_s = prof["reduce_ms"] / max(prof["reduce_launches"], 1) / 1e3
     achieved = alg_bytes / sweep_avg_s / 1e9 if sweep_avg_s > 0 else None
@@ -286,14 +292,15 @@ def main():
     peak_src = "measured" if peak else "fallback"
     if not peak:
         peak = 6800.0
-    reduce_bytes = 8 * S + 12 * g.n_vars + 4  # per launch: slot index + gathered lambda; offsets, target, result
     roofline = {"bound": "hbm", "kernel": "fdog_jit_fwd / fdog_jit_bwd (shape-specialised update sweeps)",
-                "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak if achieved else None,
-                "traffic": sweep_traffic(), "alg_bytes_per_launch": alg_bytes,
-                "avg_launch_us": sweep_avg_s * 1e6, "launches": prof["sweep_launches"],
+                "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": sweep_traffic(),
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_us": sweep_avg_s * 1e6,
+                "launches": prof["sweep_launches"],
                 "deferred_sum_kernel": {"avg_launch_us": reduce_avg_s * 1e6, "alg_bytes_per_launch": reduce_bytes,
-                                        "achieved_gbs": reduce_bytes / reduce_avg_s / 1e9 if reduce_avg_s else None}}
+                                        "achieved_gbs": reduce_bytes / reduce_avg_s / 1e9 if reduce_avg_s else None,
+                                        "variables": kp["work_vars"]},
+                "tile_local_variables": kp["local_vars"]}
     launches = prof["kernel_launches"] - launches0
 
     # ---- end to end through the public API from host buffers ------------------

@@ -142,12 +142,13 @@ int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed);
  * with shape-specialised kernels, covering *jit_tiles tiles of 32 BDDs;
  * *static_tiles tiles run the generic kernels; *local_vars variables have all
  * their copies in one tile, so the update sweep forms their deferred terms
- * (params.fuse).  If the specialised kernels could not be compiled, `note`
- * (capacity note_cap, may be NULL) receives the reason.  Any pointer may be
- * NULL.  FDOG_ESTATE if not planned.
+ * (params.fuse); the deferred-sum kernel handles the other *work_vars
+ * variables, with *work_slots copies in all.  If the specialised kernels could
+ * not be compiled, `note` (capacity note_cap, may be NULL) receives the
+ * reason.  Any pointer may be NULL.  FDOG_ESTATE if not planned.
  */
 int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
-                     int64_t* local_vars, char* note, int32_t note_cap);
+                     int64_t* local_vars, int64_t* work_vars, int64_t* work_slots, char* note, int32_t note_cap);
 int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes, int32_t* vars, int32_t* lstart,
                  int32_t* lo, int32_t* hi);
 

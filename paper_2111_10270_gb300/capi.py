@@ -61,7 +61,8 @@ SIGNATURES = {
     "fdog_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i64)]),
     "fdog_fixed_vars": (ctypes.c_int, [_P, _P]),
     "fdog_kernel_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
-                                        ctypes.POINTER(_i64), ctypes.c_char_p, _i32]),
+                                        ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                        ctypes.c_char_p, _i32]),
     "fdog_row_bdd": (ctypes.c_int, [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P, _P, _P, _P]),
     "fdog_build_bdds": (ctypes.c_int, [_P, _i32, _P]),
     "fdog_reset_dual": (ctypes.c_int, [_P]),
@@ -178,12 +179,13 @@ class Instance:
         return b.value
 
     def kernel_plan(self):
-        js, jt, st, lv = _i32(), _i64(), _i64(), _i64()
+        js, jt, st, lv, wv, ws = _i32(), _i64(), _i64(), _i64(), _i64(), _i64()
         note = ctypes.create_string_buffer(2048)
         self._check(self._L.fdog_kernel_plan(self._h, ctypes.byref(js), ctypes.byref(jt), ctypes.byref(st),
-                                             ctypes.byref(lv), note, 2048), "fdog_kernel_plan")
+                                             ctypes.byref(lv), ctypes.byref(wv), ctypes.byref(ws), note, 2048),
+                    "fdog_kernel_plan")
         return {"jit_shapes": js.value, "jit_tiles": jt.value, "static_tiles": st.value, "local_vars": lv.value,
-                "note": note.value.decode(errors="replace")}
+                "work_vars": wv.value, "work_slots": ws.value, "note": note.value.decode(errors="replace")}
 
     def fixed_vars(self):
         f = np.zeros(self.n_vars, np.int8)

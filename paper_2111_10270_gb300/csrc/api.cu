@@ -217,6 +217,8 @@ int allocate_and_upload(fdog_instance* inst) {
     };
     two(&b.var_prefix, static_cast<int32_t>(n));
     b.vars_total = static_cast<int32_t>(n);
+    two(&b.tile_all_prefix, static_cast<int32_t>(nt));
+    b.tiles_all_total = static_cast<int32_t>(nt);
     two(&b.work_prefix, static_cast<int32_t>(d.work.size()));
     b.work_total = static_cast<int32_t>(d.work.size());
     for (int c = 0; c < kNumClasses; ++c) b.has_local[c] = d.cls_has_local[c];
@@ -442,6 +444,8 @@ int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream) {
     inst->cfg.prof = &inst->prof;
     e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_ctl), sizeof(InstCtl));
     if (e != cudaSuccess) { cudaGetLastError(); inst->host_ctl = nullptr; return FDOG_ENOMEM; }
+    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_x), std::max<size_t>(inst->n_vars, 1));
+    if (e != cudaSuccess) { cudaGetLastError(); inst->host_x = nullptr; return FDOG_ENOMEM; }
     rc = allocate_and_upload(inst);
     if (rc != FDOG_OK) return rc;
     rc = reset_dual_state(inst);
@@ -461,11 +465,13 @@ int fdog_plan(fdog_instance* inst, int64_t* device_bytes) {
 }
 
 int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tiles, int64_t* static_tiles,
-                     int64_t* local_vars, char* note, int32_t note_cap) {
+                     int64_t* local_vars, int64_t* work_vars, int64_t* work_slots, char* note, int32_t note_cap) {
     if (!inst) return FDOG_EINVAL;
     if (!inst->planned) return FDOG_ESTATE;
     const Decomposition& d = inst->dec;
     if (local_vars) *local_vars = d.n_local_vars;
+    if (work_vars) *work_vars = static_cast<int64_t>(d.work.size());
+    if (work_slots) *work_slots = d.n_work_slots;
     if (jit_shapes) *jit_shapes = static_cast<int32_t>(jit_ids(inst).size());
     const int64_t jt = d.cls_tile_begin[kJitClass + 1] - d.cls_tile_begin[kJitClass];
     if (jit_tiles) *jit_tiles = jt;
@@ -698,34 +704,33 @@ int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used) {
         if (e != cudaSuccess) return fail_cuda(inst, e, "re-optimisation");
         ++round;
     }
-    // objective over the BDD variables on the device; presolve constants on the host
+    // objective over the BDD variables and the BDD acceptance test on the
+    // device; presolve constants on the host
     double obj_dev = 0.0;
-    std::vector<uint8_t> x(inst->n_vars, 0);
+    int32_t rejected = 0;
     if (any) {
         cudaError_t e = launch_objective(inst->batch, inst->cfg, s);
         if (e == cudaSuccess)
-            e = copy_async(inst, x.data(), inst->dev.x, inst->n_vars, cudaMemcpyDeviceToHost);
+            e = cudaMemsetAsync(reinterpret_cast<char*>(inst->dev.ctl) + offsetof(InstCtl, n_rejected), 0,
+                                sizeof(int32_t), s);
+        if (e == cudaSuccess) e = launch_accept(inst->batch, inst->cfg, s);
+        if (e == cudaSuccess) e = copy_async(inst, inst->host_x, inst->dev.x, inst->n_vars, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return fail_cuda(inst, e, "objective");
         InstCtl c;
         if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
         obj_dev = c.objective;
+        rejected = c.n_rejected;
     }
+    std::vector<uint8_t> x(inst->n_vars, 0);
+    if (any) std::memcpy(x.data(), inst->host_x, inst->n_vars);
     for (int32_t i = 0; i < inst->n_vars; ++i) {
         const int8_t f = inst->dec.fixed[i];
         if (f == 0 || f == 1) x[i] = static_cast<uint8_t>(f);
         else if (f == 2) x[i] = inst->cost[i] < 0 ? 1 : 0;
     }
-    inst->solution = x;
+    inst->solution = std::move(x);
     inst->objective = obj_dev + inst->dec.const_obj;
-    // exact integer feasibility check of every original row
-    int feasible = 1;
-    for (int32_t j = 0; j < inst->n_rows && feasible; ++j) {
-        int64_t sum = 0;
-        for (int64_t q = inst->row_ptr[j]; q < inst->row_ptr[j + 1]; ++q)
-            sum += static_cast<int64_t>(inst->coef[q]) * x[inst->col[q]];
-        if ((inst->sense[j] <= 0 && sum > inst->rhs[j]) || (inst->sense[j] >= 0 && sum < inst->rhs[j])) feasible = 0;
-    }
-    inst->feasible = feasible;
+    inst->feasible = rejected == 0 ? 1 : 0;
     inst->has_solution = true;
     inst->rounds = round;
     inst->iterated = false;  // the running bound of the perturbed problem is not an ILP bound
@@ -770,6 +775,7 @@ void fdog_destroy(fdog_instance* inst) {
         if (inst->arena) cudaFree(inst->arena);
         if (inst->dev.mm1) cudaFree(inst->dev.mm1);
         if (inst->host_ctl) cudaFreeHost(inst->host_ctl);
+        if (inst->host_x) cudaFreeHost(inst->host_x);
         inst->prof.release();
         cudaGetLastError();
     }

@@ -402,8 +402,14 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         }
     }
     for (int32_t i = 0; i < n_vars; ++i) {
-        if (local[i]) ++out.n_local_vars;
-        else if (out.csr_off[i + 1] > out.csr_off[i]) out.work.push_back(i);
+        const int32_t c = out.csr_off[i + 1] - out.csr_off[i];
+        if (local[i]) {
+            ++out.n_local_vars;
+        } else if (c > 0) {
+            out.work.push_back(i);
+            out.n_work_slots += c;
+            if (c > 2) out.n_work_overflow += c;
+        }
     }
     return FDOG_OK;
 }

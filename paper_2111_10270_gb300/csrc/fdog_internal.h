@@ -79,6 +79,8 @@ struct InstCtl {
     int32_t window;
     int32_t min_iters;
     int32_t since_reset;      // iterations since the stopping history was reset
+    int32_t n_rejected;       // BDDs whose row the rounded solution violates
+    int32_t pad1;
     double tol;
 };
 
@@ -165,6 +167,8 @@ struct Decomposition {
     std::vector<uint16_t> local_ent;
     std::vector<int32_t> work;      // variables left to the deferred-sum kernel
     int64_t n_local_vars = 0;
+    int64_t n_work_slots = 0;       // copies of the variables in `work`
+    int64_t n_work_overflow = 0;    // of those, list entries read from csr_pos (variables with > 2 copies)
     bool cls_has_local[kNumClasses] = {false};
     std::vector<ShapeDev> shape_dev;
     std::vector<uint16_t> tpl;

@@ -12,7 +12,7 @@
 namespace fdog {
 
 // prefix ints of a one-instance batch: per class 3 (prefix[2], first[1]) + 4 x 2
-constexpr int kPrefixInts = 3 * kNumClasses + 10;
+constexpr int kPrefixInts = 3 * kNumClasses + 12;
 
 struct DevArrays {
     InstDev* inst = nullptr;
@@ -67,6 +67,7 @@ struct fdog_instance {
     fdog::DevBatch batch;
     fdog::LaunchCfg cfg;
     fdog::InstCtl* host_ctl = nullptr;  // pinned
+    uint8_t* host_x = nullptr;          // pinned staging of the rounded solution
     fdog::Profiler prof;
     fdog::JitKernels jit;     // shape-specialised kernels of this instance's shapes
     bool jit_failed = false;  // NVRTC unavailable or failed: generic kernels only

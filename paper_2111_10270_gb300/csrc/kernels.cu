@@ -269,6 +269,34 @@ __global__ void __launch_bounds__(256) round_apply_kernel(FlatArgs a) {
     }
 }
 
+// Exact feasibility of the rounded solution: each thread follows its BDD
+// along x (Def. of constraint set correspondence: x is in X_j iff its path
+// ends at TOP) and counts the BDDs that reject it.  Rows removed by presolve
+// are satisfied by construction, so this checks every row of the ILP.
+__global__ void __launch_bounds__(256) accept_kernel(FlatArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < a.total; g += warps) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        const TileDev tile = I->tiles[g - __ldg(a.prefix + ii)];
+        if (lane >= tile.n_valid) continue;
+        const ShapeDev sh = I->shapes[tile.shape];
+        const uint16_t* __restrict__ tpl = I->tpl + sh.tpl_off;
+        uint32_t node = 0;
+        bool ok = true;
+        for (int t = 0; t < sh.k && ok; ++t) {
+            const int v = I->var[static_cast<size_t>(tile.slot_base) + static_cast<size_t>(t) * kTile + lane];
+            const uint32_t code = tpl[t * sh.width + node];
+            const uint32_t next = I->x[v] ? (code >> 8) : (code & 0xFFu);
+            if (next == kCodeBot) ok = false;
+            else if (next == kCodeTop) ok = (t == sh.k - 1);
+            else node = next;
+        }
+        if (!ok) atomicAdd(&I->ctl->n_rejected, 1);
+    }
+}
+
 // c^T x over the variables inside BDDs, FP64 Neumaier with fixed chunking
 __global__ void __launch_bounds__(256) objective_kernel(LbArgs a) {
     __shared__ double ss[256], sc[256];
@@ -468,6 +496,14 @@ cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream
     if (b.objchunks_total == 0) return cudaSuccess;
     cfg.count();
     objective_kernel<<<b.objchunks_total, 256, 0, s>>>(LbArgs{b.insts, b.objchunk_prefix, b.n_inst, 0});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.tiles_all_total == 0) return cudaSuccess;
+    cfg.count();
+    accept_kernel<<<blocks_for(b.tiles_all_total, 8, cfg.num_sms * 8), 256, 0, s>>>(
+        flat(b, b.tile_all_prefix, b.tiles_all_total));
     return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ struct DevBatch {
     int32_t kmax[kNumClasses] = {};
     int32_t* var_prefix = nullptr;           // [n_inst + 1]
     int32_t vars_total = 0;
+    int32_t* tile_all_prefix = nullptr;      // [n_inst + 1] all tiles of every class
+    int32_t tiles_all_total = 0;
     int32_t* work_prefix = nullptr;          // [n_inst + 1] variables left to the deferred-sum kernel
     int32_t work_total = 0;
     bool has_local[kNumClasses] = {};        // some tile of the class has tile-local variables
@@ -88,6 +90,7 @@ cudaError_t launch_round_test(const DevBatch& b, int round, double delta, uint64
                               cudaStream_t s);
 cudaError_t launch_round_apply(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 
 // one full dual iteration (forward pass, deferred sums, backward pass,
 // deferred sums, lower bound) on every instance of the batch

@@ -184,3 +184,179 @@ def random_ilp(n: int, m: int, seed: int, max_row: int = 5, max_coef: int = 2, e
             rb.add(cols, a, 1, ax - int(rng.integers(0, 2)))
     cost = rng.standard_normal(n)
     return rb.finish(n, cost, f"rand{n}x{m}s{seed}", {"kind": "random", "hidden": xs})
+
+
+def _knn(src, dst, k):
+    """indices of the k nearest points of dst for every point of src (Euclidean)."""
+    from scipy.spatial import cKDTree
+
+    k = min(k, len(dst))
+    _, idx = cKDTree(dst).query(src, k=k)
+    return np.asarray(idx).reshape(len(src), k)
+
+
+def cell_tracking(seed: int, frames: int | None = None, det_lo: int = 200, det_hi: int = 2000, n_next: int = 5,
+                  n_div: int = 2) -> ILP:
+    """Cell-tracking-shaped 0-1 ILP (the structure of the paper's cell
+    tracking datasets, with synthetic detections).  Frames ~ U{10..80} (or the
+    given number), detections per frame ~ U{det_lo..det_hi}, points in
+    U[0,1]^2.  Variables: one per detection d, then transitions t(d -> e) to
+    the n_next nearest detections of the next frame, then one division per
+    detection into its n_div nearest next-frame detections.  Rows:
+      out-flow  sum_e t(d -> e) + div(d) - d <= 0
+      in-flow   sum_c t(c -> d) + sum_{c divides into d} div(c) - d <= 0
+      conflicts sum x <= 1 over disjoint triples of mutually close detections
+                of one frame (greedy grouping).
+    Costs N(0,1).  Seeded numpy PCG64."""
+    rng = np.random.default_rng(seed)
+    F = int(rng.integers(10, 81)) if frames is None else int(frames)
+    counts = rng.integers(det_lo, det_hi + 1, F)
+    pts = [rng.random((int(c), 2)) for c in counts]
+    det_off = np.concatenate([[0], np.cumsum(counts)])
+    n_det = int(det_off[-1])
+    # transitions and divisions
+    t_src, t_dst, dv_src, dv_dst = [], [], [], []
+    for f in range(F - 1):
+        nn = _knn(pts[f], pts[f + 1], n_next)
+        src = np.repeat(np.arange(counts[f]) + det_off[f], nn.shape[1])
+        t_src.append(src)
+        t_dst.append((nn + det_off[f + 1]).reshape(-1))
+        nd = _knn(pts[f], pts[f + 1], n_div)
+        dv_src.append(np.arange(counts[f]) + det_off[f])
+        dv_dst.append(nd + det_off[f + 1])
+    t_src = np.concatenate(t_src) if t_src else np.zeros(0, np.int64)
+    t_dst = np.concatenate(t_dst) if t_dst else np.zeros(0, np.int64)
+    dv_src = np.concatenate(dv_src) if dv_src else np.zeros(0, np.int64)
+    dv_dst = np.concatenate(dv_dst) if dv_dst else np.zeros((0, n_div), np.int64)
+    n_t = len(t_src)
+    n_dv = len(dv_src)
+    t_var = n_det + np.arange(n_t)
+    dv_var = n_det + n_t + np.arange(n_dv)
+    n = n_det + n_t + n_dv
+    cols_list, coef_list, len_list = [], [], []
+    # out-flow rows: detections with successors, [d, its n_next transitions, its division]
+    has_out = np.zeros(n_det, bool)
+    has_out[dv_src] = True
+    if n_t:
+        k_next = n_t // max(len(dv_src), 1)
+        out_d = dv_src  # detections of every frame but the last, in order
+        block = np.concatenate([out_d[:, None], t_var.reshape(len(out_d), k_next), dv_var[:, None]], axis=1)
+        cols_list.append(block.reshape(-1))
+        coef_list.append(np.tile(np.concatenate([[-1], np.ones(k_next + 1, np.int64)]), len(out_d)))
+        len_list.append(np.full(len(out_d), k_next + 2))
+    # in-flow rows: [d, incoming transitions and divisions in ascending variable order]
+    dst = np.concatenate([t_dst, dv_dst.reshape(-1)])
+    src_var = np.concatenate([t_var, np.repeat(dv_var, dv_dst.shape[1] if n_dv else 0)])
+    order = np.lexsort((src_var, dst))
+    dst, src_var = dst[order], src_var[order]
+    in_cnt = np.bincount(dst, minlength=n_det)
+    in_d = np.nonzero(in_cnt)[0]
+    starts = np.concatenate([[0], np.cumsum(in_cnt[in_d])])
+    row_cols = np.empty(len(in_d) + len(src_var), np.int64)
+    row_coef = np.ones(len(row_cols), np.int64)
+    pos = starts[:-1] + np.arange(len(in_d))  # slot of d in each row
+    row_cols[pos] = in_d
+    row_coef[pos] = -1
+    mask = np.ones(len(row_cols), bool)
+    mask[pos] = False
+    row_cols[mask] = src_var
+    cols_list.append(row_cols)
+    coef_list.append(row_coef)
+    len_list.append(in_cnt[in_d] + 1)
+    # conflict triples: greedy disjoint grouping of mutually close detections
+    trip = []
+    for f in range(F):
+        c = int(counts[f])
+        if c < 3:
+            continue
+        nn = _knn(pts[f], pts[f], 3)
+        used = np.zeros(c, bool)
+        for a in range(c):
+            b_, c_ = int(nn[a, 1]), int(nn[a, 2])
+            if used[a] or used[b_] or used[c_] or len({a, b_, c_}) < 3:
+                continue
+            used[[a, b_, c_]] = True
+            trip.append(sorted([a + det_off[f], b_ + det_off[f], c_ + det_off[f]]))
+    if trip:
+        cols_list.append(np.asarray(trip, np.int64).reshape(-1))
+        coef_list.append(np.ones(3 * len(trip), np.int64))
+        len_list.append(np.full(len(trip), 3))
+    lens = np.concatenate(len_list)
+    row_ptr = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    n_rows = len(lens)
+    sense = np.full(n_rows, -1, np.int8)
+    rhs = np.zeros(n_rows, np.int64)
+    if trip:
+        rhs[-len(trip):] = 1
+    cost = rng.standard_normal(n)
+    return ILP(n, cost, row_ptr, np.concatenate(cols_list).astype(np.int32),
+               np.concatenate(coef_list).astype(np.int32), sense, rhs, name=f"cell{seed}",
+               meta={"kind": "cell", "frames": F, "detections": n_det, "transitions": n_t, "divisions": n_dv})
+
+
+def qap(seed: int, n_left: int = 500, n_right: int = 1000, n_cand: int = 20, k_nn: int = 10,
+        sparse: bool = False) -> ILP:
+    """QAP-shaped graph matching as a 0-1 ILP.  Left and right nodes are
+    points in U[0,1]^2; each left node p has n_cand distinct uniformly drawn
+    right candidates a, with an assignment variable x_{p,a}.  Rows: sum_a
+    x_{p,a} <= 1 per left node and sum_p x_{p,a} <= 1 per right node (rows with
+    fewer than two variables dropped).  Quadratic terms: for every unordered
+    pair {p, q} with q among the k_nn nearest left nodes of p, every candidate
+    pair (a, b), a != b, gets a product variable z = x_{p,a} x_{q,b},
+    linearised as  z - x_{p,a} <= 0,  z - x_{q,b} <= 0,
+    x_{p,a} + x_{q,b} - z <= 1  (with sparse=True only pairs with b among the
+    k_nn nearest right nodes of a).  All costs N(0,1).  Seeded PCG64."""
+    rng = np.random.default_rng(seed)
+    L = rng.random((n_left, 2))
+    R = rng.random((n_right, 2))
+    n_cand = min(n_cand, n_right)
+    cand = np.stack([rng.choice(n_right, n_cand, replace=False) for _ in range(n_left)])
+    x_index = np.arange(n_left * n_cand).reshape(n_left, n_cand)
+    nn = _knn(L, L, k_nn + 1)[:, 1:]
+    pp = np.repeat(np.arange(n_left), nn.shape[1])
+    qq = nn.reshape(-1)
+    keep = pp != qq
+    pr = np.unique(np.stack([np.minimum(pp, qq), np.maximum(pp, qq)], axis=1)[keep], axis=0)
+    A = cand[pr[:, 0]][:, :, None]  # [pairs, n_cand, 1]
+    B = cand[pr[:, 1]][:, None, :]  # [pairs, 1, n_cand]
+    ok = A != B
+    if sparse:
+        rnn = _knn(R, R, k_nn + 1)[:, 1:]
+        near = np.zeros((n_right, n_right), bool)
+        near[np.repeat(np.arange(n_right), rnn.shape[1]), rnn.reshape(-1)] = True
+        ok &= near[A, B]
+    pi, ia, ib = np.nonzero(ok)
+    zs = np.stack([x_index[pr[pi, 0], ia], x_index[pr[pi, 1], ib]], axis=1)
+    n_x = n_left * n_cand
+    n_z = len(zs)
+    n = n_x + n_z
+    # rows: left uniqueness, right uniqueness (>= 2 variables), three rows per product
+    left_cols = x_index.reshape(-1)
+    left_len = np.full(n_left, n_cand)
+    xr = cand.reshape(-1)  # right node of every x
+    order = np.lexsort((left_cols, xr))
+    r_cnt = np.bincount(xr, minlength=n_right)
+    big = r_cnt >= 2
+    # variables of right node a, ascending, for the nodes with >= 2 of them
+    xs_sorted = left_cols[order]
+    node_of = xr[order]
+    sel = big[node_of]
+    right_cols = xs_sorted[sel]
+    right_len = r_cnt[big]
+    z = n_x + np.arange(n_z)
+    prod_cols = np.stack([zs[:, 0], z, zs[:, 1], z, zs[:, 0], zs[:, 1], z], axis=1).reshape(-1)
+    prod_coef = np.tile(np.array([-1, 1, -1, 1, 1, 1, -1], np.int64), n_z)
+    prod_len = np.tile(np.array([2, 2, 3]), n_z)
+    lens = np.concatenate([left_len, right_len, prod_len])
+    row_ptr = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    cols = np.concatenate([left_cols, right_cols, prod_cols]).astype(np.int32)
+    coef = np.concatenate([np.ones(len(left_cols) + len(right_cols), np.int64), prod_coef]).astype(np.int32)
+    n_rows = len(lens)
+    sense = np.full(n_rows, -1, np.int8)
+    rhs = np.ones(n_rows, np.int64)
+    rhs[n_left + len(right_len):] = np.tile(np.array([0, 0, 1]), n_z)
+    cost = rng.standard_normal(n)
+    return ILP(n, cost, row_ptr, cols, coef, sense, rhs, name=f"qap{n_left}x{n_right}s{seed}",
+               meta={"kind": "qap", "products": n_z, "pairs": len(pr)})

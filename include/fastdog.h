@@ -280,6 +280,32 @@ int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* swee
                       double* reduce_ms, int64_t* kernel_launches);
 
 /*
+ * Ragged batching.  A batch runs several built instances (same device) as one
+ * flat index space of BDD tiles and variables: every kernel launch covers all
+ * members, so many small instances fill the GPU as one large one would.  Each
+ * member follows its own schedule -- Alg. 1 until its stopping rule (or
+ * max_iters iterations), then Alg. 2 -- and gets exactly the results it would
+ * get alone (all reductions are per instance in a fixed order).  Iterations
+ * run as CUDA-graph replays on cuda_stream when it is not NULL; the sweep
+ * kernels' warps per block are autotuned at creation when the first member's
+ * params.block_threads is 0.  Members stay owned by the caller and must
+ * outlive the batch; an instance may belong to one batch call at a time.
+ *
+ * fdog_batch_solve: Alg. 1 then Alg. 2 for every member from its current
+ * state; per member (arrays of n entries, each may be NULL) the dual
+ * iterations run, the rounding rounds used and FDOG_OK / FDOG_ENOCONVERGE.
+ * Solutions are then available through fdog_solution on each member.
+ * fdog_batch_info: the chosen warps per block, iterations per graph replay,
+ * and the batch's kernel launches so far.
+ */
+typedef struct fdog_batch fdog_batch;
+int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream, fdog_batch** out);
+int fdog_batch_solve(fdog_batch* batch, int32_t max_iters, int32_t* iters, int32_t* rounds, int32_t* status);
+int fdog_batch_info(fdog_batch* batch, int32_t* warps_per_block, int32_t* chunk, int64_t* kernel_launches);
+const char* fdog_batch_last_error(const fdog_batch* batch);
+void fdog_batch_destroy(fdog_batch* batch);
+
+/*
  * Allocation-free lower-bound reduction (the paper has no counterpart: this
  * serves callers that cannot allocate device memory -- plug-ins whose host
  * framework owns every device allocation through its own pool, and real-time

@@ -81,6 +81,11 @@ SIGNATURES = {
     "fdog_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "fdog_info": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "fdog_batch_create": (ctypes.c_int, [_P, _i32, _P, ctypes.POINTER(_P)]),
+    "fdog_batch_solve": (ctypes.c_int, [_P, _i32, _P, _P, _P]),
+    "fdog_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "fdog_batch_last_error": (ctypes.c_char_p, [_P]),
+    "fdog_batch_destroy": (None, [_P]),
     "fdog_bound_reduce_noalloc": (ctypes.c_int, [_P, _i64, _f64, _P, _P]),
     "fdog_last_error": (ctypes.c_char_p, [_P]),
     "fdog_destroy": (None, [_P]),
@@ -294,3 +299,46 @@ class Instance:
         self._check(self._L.fdog_info(self._h, *[ctypes.byref(x) for x in v]), "fdog_info")
         keys = ("n_vars", "n_bdds", "n_slots", "n_nodes", "device_bytes")
         return dict(zip(keys, (x.value for x in v)))
+
+
+class Batch:
+    """Owns one fdog_batch* over built Instances (which must outlive it)."""
+
+    def __init__(self, instances, stream=None):
+        L = lib()
+        self._L = L
+        self.instances = list(instances)
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        arr = (ctypes.c_void_p * len(self.instances))(*[i._h.value for i in self.instances])
+        h = ctypes.c_void_p()
+        rc = L.fdog_batch_create(arr, len(self.instances), ctypes.c_void_p(stream) if stream else None,
+                                 ctypes.byref(h))
+        if rc != FDOG_OK:
+            raise FdogError(rc, "fdog_batch_create")
+        self._h = h
+
+    def solve(self, max_iters: int):
+        n = len(self.instances)
+        iters = np.zeros(n, np.int32)
+        rounds = np.zeros(n, np.int32)
+        status = np.zeros(n, np.int32)
+        rc = self._L.fdog_batch_solve(self._h, max_iters, _ptr(iters), _ptr(rounds), _ptr(status))
+        if rc != FDOG_OK:
+            detail = self._L.fdog_batch_last_error(self._h)
+            raise FdogError(rc, "fdog_batch_solve", detail.decode() if detail else "")
+        return iters, rounds, status
+
+    def info(self):
+        w, c, k = _i32(), _i32(), _i64()
+        self._L.fdog_batch_info(self._h, ctypes.byref(w), ctypes.byref(c), ctypes.byref(k))
+        return {"warps_per_block": w.value, "chunk": c.value, "kernel_launches": k.value}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.fdog_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

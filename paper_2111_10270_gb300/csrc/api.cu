@@ -2,12 +2,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
 #include <vector>
 
+#include "engine.h"
 #include "instance.h"
 #include "kernels.h"
 
@@ -189,6 +191,11 @@ int allocate_and_upload(fdog_instance* inst) {
     h.n_obj_chunks = static_cast<int32_t>(nobj);
     h.omega = static_cast<float>(inst->params.omega);
     h.const_lb = d.const_lb;
+    h.alpha = inst->params.alpha;
+    h.delta0 = inst->params.delta;
+    h.seed = inst->params.seed;
+    h.stop_param = inst->params.tol > 0 ? 1 : 0;
+    h.reopt_iters = inst->params.rounding_dual_iters;
     inst->hdesc = h;
 
     // self-batch prefix arrays: per class (prefix[2], first[1]), then vars, slots, chunks, objective chunks
@@ -250,6 +257,28 @@ int allocate_and_upload(fdog_instance* inst) {
     return FDOG_OK;
 }
 
+// The engine and one-member view behind an instance's own calls.
+int own_engine(fdog_instance* inst, Engine** eng, BatchView** view) {
+    if (!inst->engine) {
+        inst->engine = new (std::nothrow) Engine();
+        inst->self_view = new (std::nothrow) BatchView();
+        if (!inst->engine || !inst->self_view) return FDOG_ENOMEM;
+    }
+    Engine& e = *inst->engine;
+    e.device = inst->device;
+    e.stream = inst->stream;
+    e.cfg = inst->cfg;
+    e.prof = &inst->prof;
+    int rc = view_build(e, *inst->self_view, {inst});
+    if (rc != FDOG_OK) {
+        inst->last_error = e.err;
+        return rc;
+    }
+    *eng = inst->engine;
+    *view = inst->self_view;
+    return FDOG_OK;
+}
+
 int reset_dual_state(fdog_instance* inst) {
     InstCtl c{};
     const fdog_params& p = inst->params;
@@ -257,6 +286,8 @@ int reset_dual_state(fdog_instance* inst) {
     c.window = p.window;
     c.min_iters = p.min_iters;
     c.tol = p.tol;
+    c.iter_limit = 0;
+    c.delta = p.delta;
     cudaError_t e = copy_async(inst, inst->dev.ctl, &c, sizeof(c), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail_cuda(inst, e, "reset ctl");
     e = launch_init(inst->batch, inst->cfg, inst->stream);
@@ -314,6 +345,7 @@ int ensure_mm1(fdog_instance* inst) {
     if (e != cudaSuccess) { cudaGetLastError(); return FDOG_ENOMEM; }
     inst->dev.mm1 = static_cast<float*>(p);
     inst->hdesc.mm1 = inst->dev.mm1;
+    if (inst->self_view) inst->self_view->uids.clear();  // rebuild its descriptor copy on next use
     e = copy_async(inst, inst->dev.inst, &inst->hdesc, sizeof(InstDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);
     return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "descriptor update");
@@ -390,6 +422,8 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
     }
     fdog_instance* inst = new (std::nothrow) fdog_instance();
     if (!inst) return FDOG_ENOMEM;
+    static std::atomic<uint64_t> next_uid{1};
+    inst->uid = next_uid.fetch_add(1);
     try {
         inst->n_vars = n_vars;
         inst->n_rows = n_rows;
@@ -559,10 +593,16 @@ int fdog_dual_iterate(fdog_instance* inst, int32_t k, int32_t* iters_done, doubl
     InstCtl before;
     int rc = read_ctl(inst, before);
     if (rc != FDOG_OK) return rc;
-    if (inst->dec.n_bdds > 0) {
-        for (int32_t t = 0; t < k; ++t) {
-            cudaError_t e = launch_iteration(inst->batch, inst->cfg, inst->stream);
-            if (e != cudaSuccess) return fail_cuda(inst, e, "iteration");
+    if (inst->dec.n_bdds > 0 && k > 0) {
+        Engine* e;
+        BatchView* v;
+        if ((rc = own_engine(inst, &e, &v)) != FDOG_OK) return rc;
+        // the instance runs exactly k iterations unless its stopping rule fires first
+        rc = view_op(*e, *v, kOpLimit, k);
+        if (rc == FDOG_OK) rc = view_iterate(*e, *v, k);
+        if (rc != FDOG_OK) {
+            inst->last_error = e->err;
+            return rc;
         }
     }
     InstCtl after;
@@ -674,71 +714,20 @@ int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used) {
     if (!inst) return FDOG_EINVAL;
     if (!inst->built) return FDOG_ESTATE;
     DeviceGuard g(inst->device);
-    const fdog_params& p = inst->params;
-    cudaStream_t s = inst->stream;
-    int rc = addback(inst);
+    Engine* e;
+    BatchView* v;
+    int rc = own_engine(inst, &e, &v);
     if (rc != FDOG_OK) return rc;
-    const int32_t zero = 0;
-    if ((rc = set_ctl_field(inst, offsetof(InstCtl, stop_enabled), &zero, sizeof(zero))) != FDOG_OK) return rc;
-    if ((rc = set_ctl_field(inst, offsetof(InstCtl, done), &zero, sizeof(zero))) != FDOG_OK) return rc;
-    double delta = p.delta;
-    int round = 0;
-    int status = FDOG_OK;
-    const bool any = inst->dec.n_bdds > 0;
-    while (any) {
-        cudaError_t e = launch_sweep(inst->batch, kMinMarg, 0, inst->cfg, s);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(reinterpret_cast<char*>(inst->dev.ctl) + offsetof(InstCtl, n_disagree), 0,
-                                sizeof(int32_t), s);
-        if (e == cudaSuccess) e = launch_round_test(inst->batch, round, delta, p.seed, inst->cfg, s);
-        if (e != cudaSuccess) return fail_cuda(inst, e, "rounding test");
-        InstCtl c;
-        if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
-        if (c.n_disagree == 0) break;
-        if (round >= p.max_rounds) { status = FDOG_ENOCONVERGE; break; }
-        e = launch_round_apply(inst->batch, inst->cfg, s);
-        if (e != cudaSuccess) return fail_cuda(inst, e, "perturbation");
-        delta *= p.alpha;
-        for (int t = 0; t < p.rounding_dual_iters && e == cudaSuccess; ++t) e = launch_iteration(inst->batch, inst->cfg, s);
-        if (e == cudaSuccess) e = launch_addback(inst->batch, inst->cfg, s);
-        if (e != cudaSuccess) return fail_cuda(inst, e, "re-optimisation");
-        ++round;
+    std::vector<int> rounds, status;
+    rc = engine_round(*e, {inst}, &rounds, &status);
+    if (rc != FDOG_OK) {
+        inst->last_error = e->err;
+        return rc;
     }
-    // objective over the BDD variables and the BDD acceptance test on the
-    // device; presolve constants on the host
-    double obj_dev = 0.0;
-    int32_t rejected = 0;
-    if (any) {
-        cudaError_t e = launch_objective(inst->batch, inst->cfg, s);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(reinterpret_cast<char*>(inst->dev.ctl) + offsetof(InstCtl, n_rejected), 0,
-                                sizeof(int32_t), s);
-        if (e == cudaSuccess) e = launch_accept(inst->batch, inst->cfg, s);
-        if (e == cudaSuccess) e = copy_async(inst, inst->host_x, inst->dev.x, inst->n_vars, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return fail_cuda(inst, e, "objective");
-        InstCtl c;
-        if ((rc = read_ctl(inst, c)) != FDOG_OK) return rc;
-        obj_dev = c.objective;
-        rejected = c.n_rejected;
-    }
-    std::vector<uint8_t> x(inst->n_vars, 0);
-    if (any) std::memcpy(x.data(), inst->host_x, inst->n_vars);
-    for (int32_t i = 0; i < inst->n_vars; ++i) {
-        const int8_t f = inst->dec.fixed[i];
-        if (f == 0 || f == 1) x[i] = static_cast<uint8_t>(f);
-        else if (f == 2) x[i] = inst->cost[i] < 0 ? 1 : 0;
-    }
-    inst->solution = std::move(x);
-    inst->objective = obj_dev + inst->dec.const_obj;
-    inst->feasible = rejected == 0 ? 1 : 0;
-    inst->has_solution = true;
-    inst->rounds = round;
     inst->iterated = false;  // the running bound of the perturbed problem is not an ILP bound
     inst->pending_T = false;
-    const int32_t en = p.tol > 0 ? 1 : 0;
-    if ((rc = set_ctl_field(inst, offsetof(InstCtl, stop_enabled), &en, sizeof(en))) != FDOG_OK) return rc;
-    if (rounds_used) *rounds_used = round;
-    return status;
+    if (rounds_used) *rounds_used = rounds[0];
+    return status[0];
 }
 
 int fdog_solution(fdog_instance* inst, uint8_t* x, double* objective, int32_t* feasible) {
@@ -776,6 +765,8 @@ void fdog_destroy(fdog_instance* inst) {
         if (inst->dev.mm1) cudaFree(inst->dev.mm1);
         if (inst->host_ctl) cudaFreeHost(inst->host_ctl);
         if (inst->host_x) cudaFreeHost(inst->host_x);
+        delete inst->self_view;
+        delete inst->engine;
         inst->prof.release();
         cudaGetLastError();
     }

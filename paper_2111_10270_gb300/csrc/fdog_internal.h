@@ -80,9 +80,16 @@ struct InstCtl {
     int32_t min_iters;
     int32_t since_reset;      // iterations since the stopping history was reset
     int32_t n_rejected;       // BDDs whose row the rounded solution violates
+    int32_t iter_limit;       // update kernels skip the instance once iter reaches it
+    int32_t round;            // rounding: current round of Alg. 2
     int32_t pad1;
     double tol;
+    double delta;             // rounding: current perturbation strength
 };
+
+// True when the update kernels must leave the instance alone: its stopping
+// rule has fired or it has run the iterations it was given.
+#define FDOG_INACTIVE(ctl) ((ctl)->done || (ctl)->iter >= (ctl)->iter_limit)
 
 // Everything a kernel needs to know about one instance (device pointers).
 struct InstDev {
@@ -116,6 +123,11 @@ struct InstDev {
     int32_t n_work;
     float omega;
     double const_lb;
+    double alpha;            // rounding: perturbation growth
+    double delta0;           // rounding: initial perturbation strength
+    unsigned long long seed; // rounding: seed of the perturbation draws
+    int32_t stop_param;      // stopping rule enabled by the parameters
+    int32_t reopt_iters;     // rounding: Alg. 1 iterations per re-optimisation
 };
 
 struct SweepArgs {

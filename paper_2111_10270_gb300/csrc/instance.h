@@ -11,6 +11,9 @@
 
 namespace fdog {
 
+struct Engine;
+struct BatchView;
+
 // prefix ints of a one-instance batch: per class 3 (prefix[2], first[1]) + 4 x 2
 constexpr int kPrefixInts = 3 * kNumClasses + 12;
 
@@ -44,6 +47,7 @@ struct DevArrays {
 }  // namespace fdog
 
 struct fdog_instance {
+    uint64_t uid = 0;  // process-unique id (views compare ids, not addresses)
     // the ILP as given (copied at create)
     int32_t n_vars = 0;
     int32_t n_rows = 0;
@@ -83,6 +87,11 @@ struct fdog_instance {
     double objective = 0.0;
     int32_t feasible = 0;
     int32_t rounds = 0;
+    bool noconverge = false;
+
+    // the engine that runs this instance's own calls, and its one-member view
+    fdog::Engine* engine = nullptr;
+    fdog::BatchView* self_view = nullptr;
 
     int64_t h2d_bytes = 0;  // host-to-device bytes copied by the library for this instance
     int64_t d2h_bytes = 0;

@@ -52,7 +52,7 @@ __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
     for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
         const int ii = fdog_find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
-        if (MODE <= 1 && I->ctl->done) continue;
+        if (MODE <= 1 && FDOG_INACTIVE(I->ctl)) continue;
         const int ti = __ldg(a.first + ii) + (g - __ldg(a.prefix + ii));
         const TileDev tile = I->tiles[ti];
         const int jit = I->shapes[tile.shape].jit;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
     if (g >= a.total) return;
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
-    if (I->ctl->done) return;
+    if (FDOG_INACTIVE(I->ctl)) return;
     const int i = I->work[g - __ldg(a.prefix + ii)];  // variables with copies in several tiles
     const int2 r = reinterpret_cast<const int2*>(I->vrec)[i];
     const float* __restrict__ lam = I->lam;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     InstCtl* ctl = I->ctl;
-    if (a.target == kLbIterate && ctl->done) return;
+    if (a.target == kLbIterate && FDOG_INACTIVE(ctl)) return;
     const int c = g - __ldg(a.prefix + ii);
     const int t = c * kLbChunk + threadIdx.x;
     double s = t < I->n_tiles ? I->tile_lb[t] : 0.0, cp = 0.0;
@@ -213,9 +213,6 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 
 struct RoundArgs {
     FlatArgs f;
-    int32_t round;
-    double delta;
-    uint64_t seed;
 };
 
 // Alg. 2 per variable: agreement test on M_ij and the perturbation of this round
@@ -238,16 +235,19 @@ __global__ void __launch_bounds__(256) round_test_kernel(RoundArgs a) {
         const int cnt = e - b;
         if (!(npos == cnt || nneg == cnt)) atomicAdd(&I->ctl->n_disagree, 1);
         I->x[i] = sum < 0.f ? 1 : 0;
-        const uint64_t h = mix64(a.seed ^ (static_cast<uint64_t>(static_cast<uint32_t>(a.round)) << 32) ^
+        const int round = I->ctl->round;
+        const double delta = I->ctl->delta;
+        const uint64_t h = mix64(static_cast<uint64_t>(I->seed) ^
+                                 (static_cast<uint64_t>(static_cast<uint32_t>(round)) << 32) ^
                                  static_cast<uint64_t>(static_cast<uint32_t>(i)));
         const double r = 2.0 * (static_cast<double>(h >> 11) * 0x1.0p-53) - 1.0;
         double p;
-        if (npos == cnt) p = a.delta;
-        else if (nneg == cnt) p = -a.delta;
-        else if (nzero == cnt) p = r * a.delta;
+        if (npos == cnt) p = delta;
+        else if (nneg == cnt) p = -delta;
+        else if (nzero == cnt) p = r * delta;
         else {
             const double sg = sum > 0.f ? 1.0 : (sum < 0.f ? -1.0 : (r >= 0.0 ? 1.0 : -1.0));
-            p = sg * fabs(r) * a.delta;
+            p = sg * fabs(r) * delta;
         }
         I->pert[i] = static_cast<float>(p);
     }
@@ -333,6 +333,45 @@ __global__ void __launch_bounds__(256) objective_kernel(LbArgs a) {
             ctl->obj_ticket = 0;
         }
     }
+}
+
+// Control-block operations, one thread per instance of the batch.
+__global__ void instance_op_kernel(const InstDev* insts, int n, int op, int arg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const InstDev& I = insts[i];
+    InstCtl* c = I.ctl;
+    switch (op) {
+        case kOpLimit: c->iter_limit = c->iter + arg; break;
+        case kOpLimitReopt: c->iter_limit = c->iter + I.reopt_iters; break;
+        case kOpRoundBegin:
+            c->stop_enabled = 0; c->done = 0; c->round = 0; c->delta = I.delta0; c->n_disagree = 0;
+            break;
+        case kOpRoundNext: c->round += 1; c->delta *= I.alpha; break;
+        case kOpClearDisagree: c->n_disagree = 0; break;
+        case kOpClearRejected: c->n_rejected = 0; break;
+        case kOpStopRestore: c->stop_enabled = I.stop_param; c->done = 0; c->since_reset = 0; break;
+        default: break;
+    }
+}
+
+__global__ void status_kernel(const InstDev* insts, int n, InstStatus* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const InstCtl* c = insts[i].ctl;
+    InstStatus s;
+    s.iter = c->iter;
+    s.done = c->done;
+    s.iter_limit = c->iter_limit;
+    s.n_disagree = c->n_disagree;
+    s.n_rejected = c->n_rejected;
+    s.round = c->round;
+    s.error = c->error;
+    s.pad = 0;
+    s.lb_last = c->lb_last;
+    s.objective = c->objective;
+    s.lb_eval = c->lb_eval;
+    out[i] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -475,12 +514,11 @@ cudaError_t launch_zero_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_round_test(const DevBatch& b, int round, double delta, uint64_t seed, const LaunchCfg& cfg,
-                              cudaStream_t s) {
+cudaError_t launch_round_test(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
     if (b.vars_total == 0) return cudaSuccess;
     cfg.count();
     round_test_kernel<<<blocks_for(b.vars_total, 256, cfg.num_sms * 8), 256, 0, s>>>(
-        RoundArgs{flat(b, b.var_prefix, b.vars_total), round, delta, seed});
+        RoundArgs{flat(b, b.var_prefix, b.vars_total)});
     return cudaGetLastError();
 }
 
@@ -504,6 +542,20 @@ cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t 
     cfg.count();
     accept_kernel<<<blocks_for(b.tiles_all_total, 8, cfg.num_sms * 8), 256, 0, s>>>(
         flat(b, b.tile_all_prefix, b.tiles_all_total));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_instance_op(const DevBatch& b, int op, int arg, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.n_inst == 0) return cudaSuccess;
+    cfg.count();
+    instance_op_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst, op, arg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status(const DevBatch& b, InstStatus* dev_out, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.n_inst == 0) return cudaSuccess;
+    cfg.count();
+    status_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst, dev_out);
     return cudaGetLastError();
 }
 

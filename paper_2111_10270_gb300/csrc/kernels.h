@@ -86,8 +86,27 @@ cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg
 cudaError_t launch_init(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_addback(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_zero_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
-cudaError_t launch_round_test(const DevBatch& b, int round, double delta, uint64_t seed, const LaunchCfg& cfg,
-                              cudaStream_t s);
+cudaError_t launch_round_test(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+
+// per-instance control-block operations (instance_op_kernel)
+enum InstanceOp : int {
+    kOpLimit = 0,          // iter_limit = iter + arg
+    kOpRoundBegin = 1,     // rounding state: stop rule off, round 0, delta = delta0
+    kOpRoundNext = 2,      // round += 1, delta *= alpha
+    kOpClearDisagree = 3,
+    kOpClearRejected = 4,
+    kOpStopRestore = 5,    // stopping rule back to the parameters, stop history cleared
+    kOpLimitReopt = 6,     // iter_limit = iter + the instance's re-optimisation iterations
+};
+
+// snapshot of one instance's control block (status_kernel)
+struct InstStatus {
+    int32_t iter, done, iter_limit, n_disagree, n_rejected, round, error, pad;
+    double lb_last, objective, lb_eval;
+};
+
+cudaError_t launch_instance_op(const DevBatch& b, int op, int arg, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_status(const DevBatch& b, InstStatus* dev_out, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_round_apply(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);

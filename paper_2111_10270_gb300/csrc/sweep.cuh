@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
         const int ii = find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
-            if (I->ctl->done) continue;  // stopping rule met for this instance
+            if (FDOG_INACTIVE(I->ctl)) continue;  // stopped, or out of iterations
         }
         const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
         const ShapeDev sh = I->shapes[tile.shape];

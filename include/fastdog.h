@@ -306,6 +306,46 @@ const char* fdog_batch_last_error(const fdog_batch* batch);
 void fdog_batch_destroy(fdog_batch* batch);
 
 /*
+ * Continuous-batching server.  A worker thread on `device` keeps every
+ * admitted instance's BDDs and dual state resident and advances all of them
+ * together: each scheduling step runs a chunk of dual iterations for the
+ * instances still iterating and the rounding tests / perturbations of the
+ * others, so requests that arrive while others are on the GPU join the
+ * running set as soon as a slot (max_active) and HBM (hbm_budget bytes, from
+ * each instance's planned size) are free, in arrival order.  An instance is
+ * retired when its stopping rule (tol, window, min_iters, or max_iters
+ * iterations) has fired and rounding has agreed (or hit max_rounds); its
+ * device memory is then freed and its solution kept on the host.  Results
+ * equal those of solving each instance alone.
+ *
+ * fdog_server_submit: `inst` must be created and not built; the call plans it
+ * in the caller's thread (host work, errors returned here) and queues it;
+ * ownership moves to the server until fdog_server_take.  *ticket identifies
+ * the request.
+ * fdog_server_poll: *state 0 queued, 1 resident, 2 done; *status FDOG_OK /
+ * FDOG_ENOCONVERGE / error of the request; *lb the running bound at
+ * retirement; *latency_s submit-to-done time (or time so far).
+ * fdog_server_wait: blocks until the request is done or timeout_s passes
+ * (FDOG_ETIMEOUT).
+ * fdog_server_take: hands a done instance back (fdog_solution works on it;
+ * free it with fdog_destroy).
+ * fdog_server_stats: queued and resident requests, completed ones, HBM in
+ * use, seconds the worker spent on device work, kernel launches.
+ * fdog_server_destroy: stops the worker and destroys instances not taken.
+ */
+typedef struct fdog_server fdog_server;
+int fdog_server_create(int32_t device, int64_t hbm_budget, int32_t max_active, int32_t max_iters, fdog_server** out);
+int fdog_server_submit(fdog_server* srv, fdog_instance* inst, uint64_t* ticket);
+int fdog_server_poll(fdog_server* srv, uint64_t ticket, int32_t* state, int32_t* status, double* lb,
+                     double* latency_s);
+int fdog_server_wait(fdog_server* srv, uint64_t ticket, double timeout_s);
+int fdog_server_take(fdog_server* srv, uint64_t ticket, fdog_instance** out);
+int fdog_server_stats(fdog_server* srv, int64_t* queued, int64_t* resident, int64_t* completed, int64_t* hbm_used,
+                      double* busy_s, int64_t* kernel_launches);
+const char* fdog_server_last_error(const fdog_server* srv);
+void fdog_server_destroy(fdog_server* srv);
+
+/*
  * Allocation-free lower-bound reduction (the paper has no counterpart: this
  * serves callers that cannot allocate device memory -- plug-ins whose host
  * framework owns every device allocation through its own pool, and real-time

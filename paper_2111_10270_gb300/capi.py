@@ -86,6 +86,16 @@ SIGNATURES = {
     "fdog_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "fdog_batch_last_error": (ctypes.c_char_p, [_P]),
     "fdog_batch_destroy": (None, [_P]),
+    "fdog_server_create": (ctypes.c_int, [_i32, _i64, _i32, _i32, ctypes.POINTER(_P)]),
+    "fdog_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "fdog_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                         ctypes.POINTER(_f64), ctypes.POINTER(_f64)]),
+    "fdog_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, _f64]),
+    "fdog_server_take": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "fdog_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                          ctypes.POINTER(_i64), ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
+    "fdog_server_last_error": (ctypes.c_char_p, [_P]),
+    "fdog_server_destroy": (None, [_P]),
     "fdog_bound_reduce_noalloc": (ctypes.c_int, [_P, _i64, _f64, _P, _P]),
     "fdog_last_error": (ctypes.c_char_p, [_P]),
     "fdog_destroy": (None, [_P]),
@@ -163,7 +173,7 @@ class Instance:
 
     def close(self):
         h = getattr(self, "_h", None)
-        if h:
+        if h and not getattr(self, "_h_owned_by_server", False):
             self._L.fdog_destroy(h)
             self._h = None
 
@@ -338,6 +348,68 @@ class Batch:
         h = getattr(self, "_h", None)
         if h:
             self._L.fdog_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Server:
+    """Owns one fdog_server*; submit() hands Instances (created, not built) to it."""
+
+    def __init__(self, device=0, hbm_budget=64 << 30, max_active=256, max_iters=500):
+        L = lib()
+        self._L = L
+        h = ctypes.c_void_p()
+        rc = L.fdog_server_create(device, hbm_budget, max_active, max_iters, ctypes.byref(h))
+        if rc != FDOG_OK:
+            raise FdogError(rc, "fdog_server_create")
+        self._h = h
+        self._owned = {}
+
+    def submit(self, inst: "Instance") -> int:
+        t = ctypes.c_uint64()
+        rc = self._L.fdog_server_submit(self._h, inst._h, ctypes.byref(t))
+        if rc != FDOG_OK:
+            detail = self._L.fdog_last_error(inst._h)
+            raise FdogError(rc, "fdog_server_submit", detail.decode() if detail else "")
+        self._owned[t.value] = inst
+        inst._h_owned_by_server = True
+        return t.value
+
+    def poll(self, ticket: int):
+        st, status, lb, lat = _i32(), _i32(), _f64(), _f64()
+        rc = self._L.fdog_server_poll(self._h, ticket, ctypes.byref(st), ctypes.byref(status), ctypes.byref(lb),
+                                      ctypes.byref(lat))
+        if rc != FDOG_OK:
+            raise FdogError(rc, "fdog_server_poll")
+        return {"state": st.value, "status": status.value, "lb": lb.value, "latency_s": lat.value}
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> bool:
+        return self._L.fdog_server_wait(self._h, ticket, timeout_s) == FDOG_OK
+
+    def take(self, ticket: int) -> "Instance":
+        h = ctypes.c_void_p()
+        rc = self._L.fdog_server_take(self._h, ticket, ctypes.byref(h))
+        if rc != FDOG_OK:
+            raise FdogError(rc, "fdog_server_take")
+        inst = self._owned.pop(ticket)
+        inst._h_owned_by_server = False
+        return inst
+
+    def stats(self):
+        v = [_i64(), _i64(), _i64(), _i64(), _f64(), _i64()]
+        self._L.fdog_server_stats(self._h, *[ctypes.byref(x) for x in v])
+        keys = ("queued", "resident", "completed", "hbm_used", "busy_s", "kernel_launches")
+        return dict(zip(keys, (x.value for x in v)))
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.fdog_server_destroy(h)  # destroys instances not taken
+            for inst in self._owned.values():
+                inst._h = None
+            self._owned.clear()
             self._h = None
 
     def __del__(self):

@@ -279,6 +279,33 @@ int own_engine(fdog_instance* inst, Engine** eng, BatchView** view) {
     return FDOG_OK;
 }
 
+// Frees the instance's device memory; its plan, parameters and last solution
+// stay on the host (a later fdog_build_bdds uploads it again).
+int release_device(fdog_instance* inst) {
+    if (!inst->built) return FDOG_OK;
+    DeviceGuard g(inst->device);
+    cudaStreamSynchronize(inst->stream);
+    delete inst->self_view;
+    inst->self_view = nullptr;
+    delete inst->engine;
+    inst->engine = nullptr;
+    if (inst->arena) cudaFree(inst->arena);
+    if (inst->dev.mm1) cudaFree(inst->dev.mm1);
+    if (inst->host_ctl) cudaFreeHost(inst->host_ctl);
+    if (inst->host_x) cudaFreeHost(inst->host_x);
+    inst->prof.release();
+    cudaGetLastError();
+    inst->arena = nullptr;
+    inst->arena_bytes = 0;
+    inst->host_ctl = nullptr;
+    inst->host_x = nullptr;
+    inst->dev = DevArrays();
+    inst->built = false;
+    inst->pending_T = false;
+    inst->iterated = false;
+    return FDOG_OK;
+}
+
 int reset_dual_state(fdog_instance* inst) {
     InstCtl c{};
     const fdog_params& p = inst->params;

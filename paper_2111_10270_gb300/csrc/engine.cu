@@ -14,10 +14,6 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr int kPhaseDual = 0;
-constexpr int kPhaseTest = 1;
-constexpr int kPhaseReopt = 2;
-constexpr int kPhaseDone = 3;
 
 }  // namespace
 
@@ -117,7 +113,9 @@ int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& membe
            [](fdog_instance* m) { return static_cast<int32_t>(m->dec.tiles.size()); });
     prefix(&b.work_prefix, &b.work_total, [](fdog_instance* m) { return static_cast<int32_t>(m->dec.work.size()); });
     if (!ids.empty()) {
-        int rc = jit_kernels(ids, b.jit, e.err);
+        // a server keeps one module for every shape it has seen, so that views
+        // of changing member sets do not each need a compile
+        int rc = jit_kernels(e.jit_universe.empty() ? ids : e.jit_universe, b.jit, e.err);
         if (rc != FDOG_OK) return rc;
     }
     cudaError_t ce = cudaMemcpyAsync(v.dev, img.data(), bytes, cudaMemcpyHostToDevice, e.stream);
@@ -297,106 +295,138 @@ int finish_all(Engine& e, BatchView& v, const std::vector<int>& noconv) {
 
 }  // namespace
 
-int engine_solve(Engine& e, const std::vector<fdog_instance*>& members, int max_iters, std::vector<int>* iters,
-                 std::vector<int>* rounds, std::vector<int>* status) {
-    const int n = static_cast<int>(members.size());
-    std::vector<int> phase(n, max_iters > 0 ? kPhaseDual : kPhaseTest), noconv(n, 0), start_iter(n, 0),
-        dual_iters(n, 0);
-    std::vector<fdog_instance*> no_bdds;  // nothing to iterate: straight to rounding
-    for (int i = 0; i < n; ++i)
-        if (members[i]->dec.n_bdds == 0 && phase[i] == kPhaseDual) {
-            phase[i] = kPhaseTest;
-            no_bdds.push_back(members[i]);
-        }
-    BatchView& all = e.v_all;
-    BatchView& iterating = e.v_iter;
-    BatchView& moving = e.v_move;
-    BatchView& testing = e.v_test;
-    int rc = view_build(e, all, members);
+int engine_admit(Engine& e, std::vector<Member>& ms, size_t first, int max_iters) {
+    std::vector<fdog_instance*> fresh, no_bdds, test_now;
+    for (size_t i = first; i < ms.size(); ++i) {
+        Member& m = ms[i];
+        m.phase = max_iters > 0 ? kPhaseDual : kPhaseTest;
+        if (m.inst->dec.n_bdds == 0 && m.phase == kPhaseDual) m.phase = kPhaseTest;
+        fresh.push_back(m.inst);
+        if (m.phase == kPhaseTest) (max_iters > 0 ? no_bdds : test_now).push_back(m.inst);
+    }
+    if (fresh.empty()) return FDOG_OK;
+    BatchView& v = e.v_move;
+    int rc = view_build(e, v, fresh);
     if (rc != FDOG_OK) return rc;
     std::vector<InstStatus> st;
-    if ((rc = view_status(e, all, st)) != FDOG_OK) return rc;
-    for (int i = 0; i < n; ++i) start_iter[i] = st[i].iter;
-    if (max_iters > 0) {
-        if ((rc = view_op(e, all, kOpLimit, max_iters)) != FDOG_OK) return rc;
-        if (!no_bdds.empty()) {
-            if ((rc = view_build(e, moving, no_bdds)) != FDOG_OK) return rc;
-            if ((rc = view_op(e, moving, kOpRoundBegin, 0)) != FDOG_OK) return rc;
-        }
-    } else {
-        if ((rc = addback_all(e, all)) != FDOG_OK) return rc;
-        if ((rc = view_op(e, all, kOpRoundBegin, 0)) != FDOG_OK) return rc;
+    if ((rc = view_status(e, v, st)) != FDOG_OK) return rc;
+    for (size_t i = first; i < ms.size(); ++i) ms[i].start_iter = st[i - first].iter;
+    if (max_iters > 0 && (rc = view_op(e, v, kOpLimit, max_iters)) != FDOG_OK) return rc;
+    // members with nothing to iterate start rounding at once
+    if (!no_bdds.empty()) {
+        if ((rc = view_build(e, v, no_bdds)) != FDOG_OK) return rc;
+        if ((rc = view_op(e, v, kOpRoundBegin, 0)) != FDOG_OK) return rc;
     }
-    for (;;) {
-        std::vector<fdog_instance*> it_set;
-        for (int i = 0; i < n; ++i)
-            if (phase[i] == kPhaseDual || phase[i] == kPhaseReopt) it_set.push_back(members[i]);
-        if (!it_set.empty()) {
-            if ((rc = view_build(e, iterating, it_set)) != FDOG_OK) return rc;
-            if ((rc = view_iterate(e, iterating, e.chunk)) != FDOG_OK) return rc;
-            for (fdog_instance* m : it_set) { m->pending_T = true; m->iterated = true; }
-        }
-        if ((rc = view_status(e, all, st)) != FDOG_OK) return rc;
-        // dual phase finished (stopping rule or iteration budget): add back, start Alg. 2;
-        // re-optimisation finished: add back, test again
-        std::vector<fdog_instance*> to_begin, to_test;
-        for (int i = 0; i < n; ++i) {
-            const bool out_of_iters = st[i].done || st[i].iter >= st[i].iter_limit;
-            if (phase[i] == kPhaseDual && out_of_iters) {
-                dual_iters[i] = st[i].iter - start_iter[i];
-                to_begin.push_back(members[i]);
-                phase[i] = kPhaseTest;
-            } else if (phase[i] == kPhaseReopt && out_of_iters) {
-                to_test.push_back(members[i]);
-                phase[i] = kPhaseTest;
-            }
-        }
-        if (!to_begin.empty()) {
-            if ((rc = view_build(e, moving, to_begin)) != FDOG_OK) return rc;
-            if ((rc = addback_all(e, moving)) != FDOG_OK) return rc;
-            if ((rc = view_op(e, moving, kOpRoundBegin, 0)) != FDOG_OK) return rc;
-        }
-        if (!to_test.empty()) {
-            if ((rc = view_build(e, moving, to_test)) != FDOG_OK) return rc;
-            if ((rc = addback_all(e, moving)) != FDOG_OK) return rc;
-        }
-        std::vector<fdog_instance*> t_set;
-        std::vector<int> t_idx;
-        for (int i = 0; i < n; ++i)
-            if (phase[i] == kPhaseTest) { t_set.push_back(members[i]); t_idx.push_back(i); }
-        if (!t_set.empty()) {
-            if ((rc = view_build(e, testing, t_set)) != FDOG_OK) return rc;
-            std::vector<InstStatus> ts;
-            if ((rc = test_all(e, testing, ts)) != FDOG_OK) return rc;
-            std::vector<fdog_instance*> p_set;
-            for (size_t q = 0; q < t_set.size(); ++q) {
-                const int i = t_idx[q];
-                if (ts[q].n_disagree == 0 || t_set[q]->dec.n_bdds == 0) {
-                    phase[i] = kPhaseDone;
-                } else if (ts[q].round >= t_set[q]->params.max_rounds) {
-                    phase[i] = kPhaseDone;
-                    noconv[i] = 1;
-                } else {
-                    phase[i] = kPhaseReopt;
-                    p_set.push_back(t_set[q]);
-                }
-            }
-            if (!p_set.empty()) {
-                if ((rc = view_build(e, moving, p_set)) != FDOG_OK) return rc;
-                if ((rc = perturb_all(e, moving)) != FDOG_OK) return rc;
-            }
-        }
-        if (std::all_of(phase.begin(), phase.end(), [](int p) { return p == kPhaseDone; })) break;
+    // rounding only: the pending add-back of Alg. 1 first
+    if (!test_now.empty()) {
+        if ((rc = view_build(e, v, test_now)) != FDOG_OK) return rc;
+        if ((rc = addback_all(e, v)) != FDOG_OK) return rc;
+        if ((rc = view_op(e, v, kOpRoundBegin, 0)) != FDOG_OK) return rc;
     }
-    if ((rc = finish_all(e, all, noconv)) != FDOG_OK) return rc;
-    if (iters) *iters = dual_iters;
-    if (rounds || status) {
-        if (rounds) rounds->resize(n);
-        if (status) status->resize(n);
-        for (int i = 0; i < n; ++i) {
-            if (rounds) (*rounds)[i] = members[i]->rounds;
-            if (status) (*status)[i] = noconv[i] ? FDOG_ENOCONVERGE : FDOG_OK;
+    return FDOG_OK;
+}
+
+int engine_step(Engine& e, std::vector<Member>& ms) {
+    const int n = static_cast<int>(ms.size());
+    if (n == 0) return FDOG_OK;
+    std::vector<fdog_instance*> it_set, all_set;
+    for (const Member& m : ms) {
+        if (m.phase == kPhaseDone) continue;
+        all_set.push_back(m.inst);
+        if (m.phase == kPhaseDual || m.phase == kPhaseReopt) it_set.push_back(m.inst);
+    }
+    int rc;
+    if (!it_set.empty()) {
+        if ((rc = view_build(e, e.v_iter, it_set)) != FDOG_OK) return rc;
+        if ((rc = view_iterate(e, e.v_iter, e.chunk)) != FDOG_OK) return rc;
+        for (fdog_instance* m : it_set) { m->pending_T = true; m->iterated = true; }
+    }
+    std::vector<InstStatus> st;
+    std::vector<int> idx;  // member index of each entry of all_set
+    for (int i = 0; i < n; ++i)
+        if (ms[i].phase != kPhaseDone) idx.push_back(i);
+    if (all_set.empty()) return FDOG_OK;
+    if ((rc = view_build(e, e.v_all, all_set)) != FDOG_OK) return rc;
+    if ((rc = view_status(e, e.v_all, st)) != FDOG_OK) return rc;
+    // dual phase finished (stopping rule or iteration budget): add back, start Alg. 2;
+    // re-optimisation finished: add back, test again
+    std::vector<fdog_instance*> to_begin, to_test;
+    for (size_t q = 0; q < idx.size(); ++q) {
+        Member& m = ms[idx[q]];
+        const bool out_of_iters = st[q].done || st[q].iter >= st[q].iter_limit;
+        if (m.phase == kPhaseDual && out_of_iters) {
+            m.dual_iters = st[q].iter - m.start_iter;
+            to_begin.push_back(m.inst);
+            m.phase = kPhaseTest;
+        } else if (m.phase == kPhaseReopt && out_of_iters) {
+            to_test.push_back(m.inst);
+            m.phase = kPhaseTest;
         }
+    }
+    if (!to_begin.empty()) {
+        if ((rc = view_build(e, e.v_move, to_begin)) != FDOG_OK) return rc;
+        if ((rc = addback_all(e, e.v_move)) != FDOG_OK) return rc;
+        if ((rc = view_op(e, e.v_move, kOpRoundBegin, 0)) != FDOG_OK) return rc;
+    }
+    if (!to_test.empty()) {
+        if ((rc = view_build(e, e.v_move, to_test)) != FDOG_OK) return rc;
+        if ((rc = addback_all(e, e.v_move)) != FDOG_OK) return rc;
+    }
+    std::vector<fdog_instance*> t_set;
+    std::vector<int> t_idx;
+    for (int i = 0; i < n; ++i)
+        if (ms[i].phase == kPhaseTest) { t_set.push_back(ms[i].inst); t_idx.push_back(i); }
+    std::vector<fdog_instance*> finished;
+    std::vector<int> fin_noconv;
+    if (!t_set.empty()) {
+        if ((rc = view_build(e, e.v_test, t_set)) != FDOG_OK) return rc;
+        std::vector<InstStatus> ts;
+        if ((rc = test_all(e, e.v_test, ts)) != FDOG_OK) return rc;
+        std::vector<fdog_instance*> p_set;
+        for (size_t q = 0; q < t_set.size(); ++q) {
+            Member& m = ms[t_idx[q]];
+            if (ts[q].n_disagree == 0 || m.inst->dec.n_bdds == 0) {
+                m.phase = kPhaseDone;
+            } else if (ts[q].round >= m.inst->params.max_rounds) {
+                m.phase = kPhaseDone;
+                m.noconv = 1;
+            } else {
+                m.phase = kPhaseReopt;
+                p_set.push_back(m.inst);
+            }
+            if (m.phase == kPhaseDone) {
+                finished.push_back(m.inst);
+                fin_noconv.push_back(m.noconv);
+            }
+        }
+        if (!p_set.empty()) {
+            if ((rc = view_build(e, e.v_move, p_set)) != FDOG_OK) return rc;
+            if ((rc = perturb_all(e, e.v_move)) != FDOG_OK) return rc;
+        }
+    }
+    if (!finished.empty()) {
+        if ((rc = view_build(e, e.v_move, finished)) != FDOG_OK) return rc;
+        if ((rc = finish_all(e, e.v_move, fin_noconv)) != FDOG_OK) return rc;
+    }
+    return FDOG_OK;
+}
+
+int engine_solve(Engine& e, const std::vector<fdog_instance*>& members, int max_iters, std::vector<int>* iters,
+                 std::vector<int>* rounds, std::vector<int>* status) {
+    std::vector<Member> ms(members.size());
+    for (size_t i = 0; i < members.size(); ++i) ms[i].inst = members[i];
+    int rc = engine_admit(e, ms, 0, max_iters);
+    if (rc != FDOG_OK) return rc;
+    while (!std::all_of(ms.begin(), ms.end(), [](const Member& m) { return m.phase == kPhaseDone; }))
+        if ((rc = engine_step(e, ms)) != FDOG_OK) return rc;
+    const size_t n = ms.size();
+    if (iters) iters->resize(n);
+    if (rounds) rounds->resize(n);
+    if (status) status->resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        if (iters) (*iters)[i] = ms[i].dual_iters;
+        if (rounds) (*rounds)[i] = ms[i].inst->rounds;
+        if (status) (*status)[i] = ms[i].noconv ? FDOG_ENOCONVERGE : FDOG_OK;
     }
     return FDOG_OK;
 }

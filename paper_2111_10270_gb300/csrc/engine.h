@@ -42,6 +42,7 @@ struct Engine {
     LaunchCfg cfg;
     Profiler* prof = nullptr;  // optional kernel timing (graphs are not used while it is on)
     int chunk = 8;             // iterations per graph launch
+    std::vector<int> jit_universe;  // if set: the shape ids every view's specialised module covers
     InstStatus* dev_status = nullptr;
     InstStatus* host_status = nullptr;  // pinned
     int status_cap = 0;
@@ -57,6 +58,28 @@ int view_status(Engine& e, BatchView& v, std::vector<InstStatus>& out);
 int view_iterate(Engine& e, BatchView& v, int k);
 // Control-block operation on every member.
 int view_op(Engine& e, BatchView& v, int op, int arg);
+
+// Phase of an instance in the engine's state machine.
+constexpr int kPhaseDual = 0;   // Alg. 1 until the stopping rule or the iteration budget
+constexpr int kPhaseTest = 1;   // Alg. 2 agreement test due
+constexpr int kPhaseReopt = 2;  // Alg. 1 re-optimisation after a perturbation
+constexpr int kPhaseDone = 3;   // solution, objective and acceptance available
+
+struct Member {
+    fdog_instance* inst = nullptr;
+    int phase = kPhaseDual;
+    int noconv = 0;
+    int start_iter = 0;
+    int dual_iters = 0;
+};
+
+// Prepares members [first, end) of `ms`: iteration budget max_iters (0: they
+// go straight to Alg. 2, starting with the pending add-back).
+int engine_admit(Engine& e, std::vector<Member>& ms, size_t first, int max_iters);
+// One scheduling step over the members not yet done: a chunk of iterations
+// for the iterating ones, then every phase change the status allows; members
+// reaching kPhaseDone are finished (objective, acceptance, solution copied).
+int engine_step(Engine& e, std::vector<Member>& ms);
 
 // Picks the sweep kernels' warps per block for this view by timing
 // min-marginal sweeps (they write only scratch, so the dual state is untouched).

@@ -12,9 +12,10 @@ including the rounding rounds' re-optimisation), over the device-timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fastdog|reference]
 
-N > 1 runs one independent replica per GPU (the single-instance path has no
-data-parallel split without a cross-GPU exchange), so scaling
-is weak and the value is the sum over ranks divided by the slowest rank's time.
+N > 1 runs one independent replica per GPU (splitting one instance across
+GPUs would need a per-pass exchange of the deferred sums of shared
+variables), so scaling is weak and the value is the sum over ranks divided by
+the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -57,6 +58,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--max-iters", type=int, default=None, help="override the workload's iteration cap")
     ap.add_argument("--dual-only", action="store_true", help="steps without rounding (profiling runs)")
+    ap.add_argument("--batch-instances", type=int, default=64,
+                    help="cell-tracking batch size for the batched-vs-sequential section (0: skip)")
+    ap.add_argument("--serve-instances", type=int, default=48,
+                    help="requests of the serving stream replayed in the serving section (0: skip)")
+    ap.add_argument("--threads", type=int, default=min(16, os.cpu_count() or 1),
+                    help="host threads / processes for instance generation and planning")
     return ap.parse_args()
 
 
@@ -184,6 +191,182 @@ def solve(inst, max_iters, kr, dual_only=False):
     x, obj, feas = inst.solution()
     return {"iters": iters, "rounds": rounds, "lb": lb, "obj": obj, "feasible": feas, "rc": rc,
             "dual_iters": iters + rounds * kr}
+
+
+# ----------------------------------------------------------------------------
+# batched and served instance streams (host preparation shared by both)
+# ----------------------------------------------------------------------------
+def generate(fn, args, threads):
+    """Seeded instance generation in a spawn process pool (numpy work that
+    threads barely overlap)."""
+    import multiprocessing
+    from concurrent.futures import ProcessPoolExecutor
+
+    if threads <= 1 or len(args) <= 1:
+        return [fn(a) for a in args]
+    with ProcessPoolExecutor(max_workers=min(threads, len(args)),
+                             mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(fn, args))
+
+
+def plan_all(P, ilps, params, threads):
+    """Instances planned on the host in parallel (the C planner releases the
+    GIL); returns them with each one's planning seconds."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(g):
+        t0 = time.perf_counter()
+        inst = P.Instance.from_ilp(g, params)
+        inst.plan()
+        return inst, time.perf_counter() - t0
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        return list(ex.map(one, ilps))
+
+
+def pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def solve_built(inst, max_iters):
+    inst.reset()
+    n, lb = inst.iterate(max_iters)
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    return n, rounds, rc, x, obj, feas, lb
+
+
+def batched_section(torch, P, dev, stream, params, n_inst, threads):
+    """Cell-tracking-shaped batch: the same n_inst instances solved one at a
+    time (plain per-instance path) and as one ragged batch, both device
+    resident, both to the same stopping rule and rounding; instances/s of each
+    and whether every result is identical."""
+    import ilpgen
+
+    seeds = ilpgen._child_seeds(3, n_inst)
+    ilps = generate(ilpgen.cell_tracking, seeds, threads)
+    planned = plan_all(P, ilps, params, threads)
+    insts = [inst.build(dev, stream) for inst, _ in planned]
+    n_vars = sum(i.info()["n_vars"] for i in insts)
+    max_iters = 500
+
+    def sequential():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = [solve_built(i, max_iters) for i in insts]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    batch = P.Batch(insts, stream)
+
+    def batched():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in insts:
+            i.reset()
+        iters, rounds, status = batch.solve(max_iters)
+        sols = [i.solution() for i in insts]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, (iters, rounds, status, sols)
+
+    sequential()  # warm-up (graphs, modules)
+    batched()
+    t_seq, seq = sequential()
+    t_bat, (iters, rounds, status, sols) = batched()
+    same = all(seq[q][0] == iters[q] and seq[q][1] == rounds[q] and seq[q][2] == status[q]
+               and np.array_equal(seq[q][3], sols[q][0]) and seq[q][4] == sols[q][1] for q in range(n_inst))
+    feasible = sum(1 for q in range(n_inst) if sols[q][2])
+    batch.close()
+    for i in insts:
+        i.close()
+    return {
+        "workload": f"cell-tracking batch: {n_inst} instances, frames U{{10..80}}, detections/frame U{{200..2000}}, "
+                    f"seed 3 ({n_vars} variables in all)",
+        "metric": "instances/s (solve to the 1e-4 LB-gap stopping rule + perturbation rounding, device resident)",
+        "batched_instances_per_s": n_inst / t_bat, "sequential_instances_per_s": n_inst / t_seq,
+        "speedup": t_seq / t_bat, "batched_s": t_bat, "sequential_s": t_seq,
+        "results_identical": bool(same), "feasible": feasible,
+        "dual_iters_p50": pct([r[0] for r in seq], 50), "dual_iters_max": max(r[0] for r in seq),
+        "host_plan_s_p50": pct([t for _, t in planned], 50),
+    }
+
+
+def serving_section(torch, P, dev, stream, params, n_req, threads):
+    """Replays the first n_req requests of the seeded Poisson stream (200/s;
+    MRF and QAP mix) twice on planned instances: through the continuous-
+    batching server, and one at a time in arrival order (upload, solve, read
+    back, free).  Latency = result time - arrival time."""
+    import ilpgen
+
+    specs = ilpgen.serving_stream(4)[:n_req]
+    ilps = generate(ilpgen.stream_instance, specs, threads)
+    arrivals = np.array([sp["arrival"] for sp in specs]) - specs[0]["arrival"]
+    max_iters = 500
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * 0.8)
+
+    # planned once; a retired instance keeps its plan and can be served or built again
+    planned = plan_all(P, ilps, params, threads)
+    insts = [inst for inst, _ in planned]
+    plan_s = [t for _, t in planned]
+
+    def run_server():
+        srv = P.Server(dev, hbm_budget=budget, max_active=256, max_iters=max_iters)
+        l0 = srv.stats()["kernel_launches"]
+        t0 = time.perf_counter()
+        tickets = []
+        for q, inst in enumerate(insts):
+            d = t0 + arrivals[q] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(inst))
+        for t in tickets:
+            if not srv.wait(t, 600.0):
+                raise RuntimeError("server request timed out")
+        lat = [srv.poll(t)["latency_s"] for t in tickets]
+        t_end = time.perf_counter()
+        res = [srv.take(t).solution() for t in tickets]
+        launches = srv.stats()["kernel_launches"] - l0
+        srv.close()
+        return lat, t_end - t0, res, launches
+
+    def run_sequential():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat, res = [], []
+        for q, inst in enumerate(insts):
+            d = t0 + arrivals[q] - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            inst.build(dev, stream)
+            inst.iterate(max_iters)
+            inst.primal_round()
+            res.append(inst.solution())
+            inst.release()
+            lat.append(time.perf_counter() - (t0 + arrivals[q]))
+        return lat, time.perf_counter() - t0, res
+
+    run_server()  # warm-up: specialised modules of the growing shape universe, graphs
+    lat_srv, t_srv, res_srv, launches = run_server()
+    lat_seq, t_seq, res_seq = run_sequential()
+    for inst in insts:
+        inst.close()
+    same = all(np.array_equal(a[0], b[0]) and a[1] == b[1] for a, b in zip(res_srv, res_seq))
+    n_vars = sum(g.n_vars for g in ilps)
+    return {
+        "workload": f"serving stream: first {n_req} of 10,000 seeded requests, Poisson 200/s, 50% MRF "
+                    f"(side U{{16..256}}, labels U{{2..8}}), 50% QAP (left U{{50..1000}}), seed 4; "
+                    f"{n_vars} variables in all",
+        "metric": "instances/s and latency from arrival to result (1e-4 LB-gap stopping rule + rounding)",
+        "server_instances_per_s": n_req / t_srv, "sequential_instances_per_s": n_req / t_seq,
+        "speedup": t_seq / t_srv,
+        "server_latency_p50_s": pct(lat_srv, 50), "server_latency_p99_s": pct(lat_srv, 99),
+        "sequential_latency_p50_s": pct(lat_seq, 50), "sequential_latency_p99_s": pct(lat_seq, 99),
+        "results_identical": bool(same), "server_kernel_launches": launches,
+        "host_plan_s_p50": pct(plan_s, 50), "host_plan_s_p99": pct(plan_s, 99),
+        "scope": "requests arrive planned (host BDD construction timed separately as host_plan_s); "
+                 "upload, solve and read-back inside the latency",
+    }
 
 
 def sweep_traffic():
@@ -331,6 +514,13 @@ def main():
                "sample": f"median of {len(rates)} single dual iterations of the full {args.workload} instance "
                          f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
 
+    # ---- batched and served instance mixes (rank 0, N = 1) ---------------------
+    batched = served = None
+    if rank == 0 and world == 1 and args.batch_instances > 0:
+        batched = batched_section(torch, P, dev, stream, params, args.batch_instances, args.threads)
+    if rank == 0 and world == 1 and args.serve_instances > 0:
+        served = serving_section(torch, P, dev, stream, params, args.serve_instances, args.threads)
+
     if rank == 0:
         last = results[-1]
         line = {
@@ -343,6 +533,7 @@ def main():
                        "l2": "inputs larger than L2 (about 590 MB resident per instance)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "batched": batched, "serving": served,
         }
         print(json.dumps(line), flush=True)
     inst.close()

@@ -360,3 +360,45 @@ def qap(seed: int, n_left: int = 500, n_right: int = 1000, n_cand: int = 20, k_n
     cost = rng.standard_normal(n)
     return ILP(n, cost, row_ptr, cols, coef, sense, rhs, name=f"qap{n_left}x{n_right}s{seed}",
                meta={"kind": "qap", "products": n_z, "pairs": len(pr)})
+
+
+def _child_seeds(seed: int, n: int) -> list[int]:
+    """n independent 63-bit seeds derived from one (numpy SeedSequence)."""
+    return [int(s.generate_state(1, np.uint64)[0] >> np.uint64(1)) for s in np.random.SeedSequence(seed).spawn(n)]
+
+
+def cell_tracking_batch(seed: int = 3, n: int = 64, **kw) -> list[ILP]:
+    """The cell-tracking-shaped batch: n instances, each drawn by
+    cell_tracking() from its own child seed (frames ~ U{10..80}, detections
+    per frame ~ U{200..2000})."""
+    return [cell_tracking(s, **kw) for s in _child_seeds(seed, n)]
+
+
+def serving_stream(seed: int = 4, n: int = 10000, rate: float = 200.0) -> list[dict]:
+    """Specs of a seeded request stream: Poisson arrivals at `rate` per second;
+    half MRF grids (side ~ U{16..256}, labels ~ U{2..8}, Potts U(0,1)), half
+    QAP (left ~ U{50..1000}, right = 2 left, candidates min(20, right)).  Each
+    spec holds its arrival time and the arguments of its generator; build the
+    instance with stream_instance(spec)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    kinds = rng.random(n) < 0.5
+    sides = rng.integers(16, 257, n)
+    labels = rng.integers(2, 9, n)
+    lefts = rng.integers(50, 1001, n)
+    seeds = _child_seeds(seed + 1, n)
+    out = []
+    for q in range(n):
+        if kinds[q]:
+            out.append({"arrival": float(t[q]), "kind": "mrf", "side": int(sides[q]), "labels": int(labels[q]),
+                        "seed": seeds[q]})
+        else:
+            out.append({"arrival": float(t[q]), "kind": "qap", "left": int(lefts[q]), "seed": seeds[q]})
+    return out
+
+
+def stream_instance(spec: dict) -> ILP:
+    if spec["kind"] == "mrf":
+        return mrf_grid(spec["side"], spec["side"], spec["labels"], spec["seed"], potts_max=1.0)
+    nl = spec["left"]
+    return qap(spec["seed"], nl, 2 * nl, min(20, 2 * nl))

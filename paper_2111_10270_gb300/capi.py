@@ -65,6 +65,7 @@ SIGNATURES = {
                                         ctypes.c_char_p, _i32]),
     "fdog_row_bdd": (ctypes.c_int, [_P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _P, _P, _P, _P]),
     "fdog_build_bdds": (ctypes.c_int, [_P, _i32, _P]),
+    "fdog_release": (ctypes.c_int, [_P]),
     "fdog_reset_dual": (ctypes.c_int, [_P]),
     "fdog_transfer_bytes": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "fdog_set_profiling": (ctypes.c_int, [_P, _i32]),
@@ -186,6 +187,11 @@ class Instance:
             stream = stream.cuda_stream
         self._check(self._L.fdog_build_bdds(self._h, device, ctypes.c_void_p(stream) if stream else None),
                     "fdog_build_bdds")
+        return self
+
+    def release(self):
+        """Frees the device memory; plan and last solution stay on the host."""
+        self._check(self._L.fdog_release(self._h), "fdog_release")
         return self
 
     def plan(self) -> int:

@@ -101,13 +101,13 @@ std::vector<int> jit_ids(const fdog_instance* inst) {
     return ids;
 }
 
-int plan(fdog_instance* inst) {
+int plan(fdog_instance* inst, bool compile_jit) {
     if (inst->planned) return FDOG_OK;
     int rc;
     try {
         rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
                                  inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(),
-                                 inst->params.jit >= 0 && !inst->jit_failed, inst->params.fuse >= 0, inst->dec,
+                                 inst->jit_failed ? -1 : inst->params.jit, inst->params.fuse >= 0, inst->dec,
                                  inst->last_error);
     } catch (const std::bad_alloc&) {
         rc = FDOG_ENOMEM;
@@ -121,13 +121,13 @@ int plan(fdog_instance* inst) {
             return FDOG_EUNSUPPORTED;
         }
     std::vector<int> ids = jit_ids(inst);
-    if (!ids.empty()) {
+    if (compile_jit && !ids.empty()) {
         std::string why;
         if (jit_compile(ids, why) != FDOG_OK) {
             // shape-specialised kernels unavailable: plan again for the generic kernels only
             inst->jit_note = why;
             inst->jit_failed = true;
-            return plan(inst);
+            return plan(inst, true);
         }
     }
     inst->planned = true;
@@ -781,6 +781,11 @@ int fdog_info(fdog_instance* inst, int64_t* n_vars, int64_t* n_bdds, int64_t* n_
         *device_bytes = static_cast<int64_t>(inst->built ? inst->arena_bytes : arena_size(inst)) +
                         (inst->dev.mm1 ? static_cast<int64_t>(sizeof(float) * inst->dec.slots_pad) : 0);
     return FDOG_OK;
+}
+
+int fdog_release(fdog_instance* inst) {
+    if (!inst) return FDOG_EINVAL;
+    return release_device(inst);
 }
 
 void fdog_destroy(fdog_instance* inst) {

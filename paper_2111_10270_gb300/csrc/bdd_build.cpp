@@ -162,7 +162,7 @@ std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) 
 
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        bool use_jit, bool fuse_local, Decomposition& out, std::string& err) {
+                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err) {
     out = Decomposition();
     out.fixed.assign(n_vars, -1);
 
@@ -238,6 +238,9 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
 
     // surviving rows: their analysis holds the final shape
     std::vector<int> shape_of_an(analyses.size(), -1);
+    std::vector<int64_t> an_count(analyses.size(), 0);
+    for (int32_t j = 0; j < n_rows; ++j)
+        if (alive[j]) an_count[row_an[j]]++;
     struct Bdd { int cls; int shape; int32_t row; };
     std::vector<Bdd> bdds;
     for (int32_t j = 0; j < n_rows; ++j) {
@@ -246,8 +249,10 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         if (shape_of_an[id] < 0) {
             const HostShape& s = analyses[id].shape;
             int cls = class_of(s.width, s.k);
-            if (use_jit && s.width <= kJitMaxW && s.k <= kJitMaxK) cls = kJitClass;
-            if (cls < 0 || (!class_is_reg(cls) && s.k > kMaxLayersSmem)) {
+            // a specialised kernel costs a compile; rare shapes stay generic in the default mode
+            const bool often = jit_mode >= 1 || an_count[id] >= kJitMinBdds;
+            if (jit_mode >= 0 && often && s.width <= kJitMaxW && s.k <= kJitMaxK) cls = kJitClass;
+            if (cls < 0 || (!class_is_reg(cls) && s.k > (class_is_seg(cls) ? kMaxLayersSeg : kMaxLayersSmem))) {
                 err = "row " + std::to_string(j) + ": BDD width " + std::to_string(s.width) + " / length " +
                       std::to_string(s.k) + " exceeds the sweep kernels' limits";
                 return FDOG_EUNSUPPORTED;
@@ -365,7 +370,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
             out.vrec[2 * i + 1] = c;
         }
     }
-    // Tile-local variables: every copy in one tile (at most four copies).  The
+    // Tile-local variables: every copy in one tile (at most four copies) of a
+    // row of at most kEpiMaxK layers.  The
     // update sweep computes their deferred term itself; the deferred-sum
     // kernel keeps the rest.  Tiles with equal local-variable patterns share
     // one pattern.
@@ -375,6 +381,7 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         std::vector<uint16_t> ent;
         for (size_t ti = 0; ti < out.tiles.size(); ++ti) {
             TileDev& t = out.tiles[ti];
+            if (out.shapes[t.shape].k > kEpiMaxK) continue;  // the sweep stages at most kEpiMaxK layers
             const int64_t lo = t.slot_base, hi = lo + static_cast<int64_t>(out.shapes[t.shape].k) * kTile;
             ent.clear();
             for (int64_t p = lo; p < hi; ++p) {

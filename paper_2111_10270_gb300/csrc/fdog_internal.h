@@ -28,12 +28,15 @@ constexpr int kRegW = 4;
 constexpr int kWidths[4] = {2, 4, 8, 16};
 constexpr int kNumWidths = 4;
 constexpr int kMaxWidth = 16;
-constexpr int kMaxLayersSmem = 256;  // longest row the shared-memory kernels take
+constexpr int kMaxLayersSmem = 256;  // longest row the staged shared-memory kernels take
+constexpr int kMaxLayersSeg = 4096;  // longest row the segmented kernels (narrow BDDs) take
+constexpr int kEpiMaxK = 16;         // longest row whose tile can form tile-local deferred terms
 constexpr int kNumStaticClasses = 2 * kNumWidths;  // (width index) x (register | smem)
 constexpr int kJitClass = kNumStaticClasses;         // shape-specialised kernels
 constexpr int kNumClasses = kNumStaticClasses + 1;
 constexpr int kJitMaxK = 16;                         // rows the shape-specialised code takes
 constexpr int kJitMaxW = 4;
+constexpr int64_t kJitMinBdds = 4096;  // jit mode 0: shapes with fewer BDDs stay on the generic kernels
 
 inline int class_of(int width, int k) {
     int wi = 0;
@@ -43,6 +46,8 @@ inline int class_of(int width, int k) {
 }
 inline int class_width(int cls) { return cls == kJitClass ? kJitMaxW : kWidths[cls / 2]; }
 inline bool class_is_reg(int cls) { return cls == kJitClass || (cls % 2) == 0; }
+// long rows of narrow BDDs: segments of kRegK layers in registers, checkpoints in shared memory
+inline bool class_is_seg(int cls) { return !class_is_reg(cls) && kWidths[cls / 2] <= kRegW; }
 
 // <jit-abi>  (this block is also compiled into the shape-specialised kernels)
 struct ShapeDev {
@@ -190,10 +195,11 @@ struct Decomposition {
 
 // Builds the decomposition: presolve, BDDs per row (shared per row
 // signature), tiles, interleaved slots and the per-variable slot lists.
-// Returns an FDOG_* status.
+// jit_mode: -1 no shape-specialised class; 0 eligible shapes with at least
+// kJitMinBdds BDDs; 1 every eligible shape.  Returns an FDOG_* status.
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        bool use_jit, bool fuse_local, Decomposition& out, std::string& err);
+                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err);
 
 // shape-specialised code (jit.cpp): process-wide shape registry and kernels
 int jit_register_shape(const HostShape& s);  // id of the shape's structure

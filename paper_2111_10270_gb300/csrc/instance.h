@@ -100,7 +100,7 @@ struct fdog_instance {
 };
 
 namespace fdog {
-int plan(fdog_instance* inst);
+int plan(fdog_instance* inst, bool compile_jit = true);
 size_t arena_size(const fdog_instance* inst);
 int fail_cuda(fdog_instance* inst, cudaError_t e, const char* where);
 cudaError_t copy_async(fdog_instance* inst, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);

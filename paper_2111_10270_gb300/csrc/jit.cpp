@@ -17,9 +17,11 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <sstream>
 #include <string>
 #include <unordered_map>
@@ -32,6 +34,8 @@ namespace fdog {
 namespace {
 
 std::mutex g_mu;
+std::condition_variable g_cv;
+std::set<std::string> g_building;  // module keys being compiled
 std::unordered_map<std::string, int> g_ids;
 std::vector<HostShape> g_shapes;
 std::map<std::string, JitKernels> g_modules;
@@ -46,33 +50,49 @@ std::string id_key(std::vector<int>& ids) {
     return key;
 }
 
-// NVRTC compile of the module for `ids` (sorted, unique); caller holds g_mu
-int compile_locked(const std::vector<int>& ids, const std::string& key, std::string& err) {
-    if (g_cubins.count(key)) return FDOG_OK;
-    const std::string src = generate_module(ids);
+// NVRTC compile of the module for `ids` (sorted, unique).  Compiles run
+// outside the registry lock, so threads planning different instances compile
+// in parallel; a thread that needs a module another thread is compiling waits
+// for it instead of compiling it again.
+int compile_module(const std::vector<int>& ids, const std::string& key, std::string& err) {
+    std::string src;
+    {
+        std::unique_lock<std::mutex> lk(g_mu);
+        g_cv.wait(lk, [&] { return !g_building.count(key); });
+        if (g_cubins.count(key)) return FDOG_OK;
+        g_building.insert(key);
+        src = generate_module(ids);
+    }
+    std::vector<char> cubin;
+    int rc = FDOG_OK;
     nvrtcProgram prog;
     if (nvrtcCreateProgram(&prog, src.c_str(), "fdog_shapes.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
         err = "nvrtcCreateProgram failed";
-        return FDOG_EUNSUPPORTED;
-    }
-    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
-    nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
-    if (r != NVRTC_SUCCESS) {
-        size_t n = 0;
-        nvrtcGetProgramLogSize(prog, &n);
-        std::string log(n, '\0');
-        nvrtcGetProgramLog(prog, &log[0]);
+        rc = FDOG_EUNSUPPORTED;
+    } else {
+        const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
+        if (nvrtcCompileProgram(prog, 3, opts) != NVRTC_SUCCESS) {
+            size_t n = 0;
+            nvrtcGetProgramLogSize(prog, &n);
+            std::string log(n, '\0');
+            nvrtcGetProgramLog(prog, &log[0]);
+            err = "NVRTC: " + log.substr(0, 2000);
+            rc = FDOG_EUNSUPPORTED;
+        } else {
+            size_t n = 0;
+            nvrtcGetCUBINSize(prog, &n);
+            cubin.resize(n);
+            nvrtcGetCUBIN(prog, cubin.data());
+        }
         nvrtcDestroyProgram(&prog);
-        err = "NVRTC: " + log.substr(0, 2000);
-        return FDOG_EUNSUPPORTED;
     }
-    size_t n = 0;
-    nvrtcGetCUBINSize(prog, &n);
-    std::vector<char> cubin(n);
-    nvrtcGetCUBIN(prog, cubin.data());
-    nvrtcDestroyProgram(&prog);
-    g_cubins.emplace(key, std::move(cubin));
-    return FDOG_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (rc == FDOG_OK) g_cubins.emplace(key, std::move(cubin));
+        g_building.erase(key);
+    }
+    g_cv.notify_all();
+    return rc;
 }
 
 std::string structure_key(const HostShape& s) {
@@ -262,8 +282,7 @@ int jit_compile(const std::vector<int>& ids_in, std::string& err) {
     if (ids_in.empty()) return FDOG_OK;
     std::vector<int> ids = ids_in;
     const std::string key = id_key(ids);
-    std::lock_guard<std::mutex> lk(g_mu);
-    return compile_locked(ids, key, err);
+    return compile_module(ids, key, err);
 }
 
 int jit_kernels(const std::vector<int>& ids_in, JitKernels& out, std::string& err) {
@@ -271,11 +290,16 @@ int jit_kernels(const std::vector<int>& ids_in, JitKernels& out, std::string& er
     if (ids_in.empty()) return FDOG_OK;
     std::vector<int> ids = ids_in;
     const std::string key = id_key(ids);
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_modules.find(key);
+        if (it != g_modules.end()) { out = it->second; return FDOG_OK; }
+    }
+    int rc = compile_module(ids, key, err);
+    if (rc != FDOG_OK) return rc;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_modules.find(key);
     if (it != g_modules.end()) { out = it->second; return FDOG_OK; }
-    int rc = compile_locked(ids, key, err);
-    if (rc != FDOG_OK) return rc;
     const std::vector<char>& cubin = g_cubins.at(key);
     cudaLibrary_t lib = nullptr;
     cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);

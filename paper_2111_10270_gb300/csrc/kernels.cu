@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(256) round_test_kernel(RoundArgs a) {
         const uint64_t h = mix64(static_cast<uint64_t>(I->seed) ^
                                  (static_cast<uint64_t>(static_cast<uint32_t>(round)) << 32) ^
                                  static_cast<uint64_t>(static_cast<uint32_t>(i)));
-        const double r = 2.0 * (static_cast<double>(h >> 11) * 0x1.0p-53) - 1.0;
+        // r uniform in [-delta, delta) (Alg. 2); the tie and conflict pushes are r * delta
+        const double r = (2.0 * (static_cast<double>(h >> 11) * 0x1.0p-53) - 1.0) * delta;
         double p;
         if (npos == cnt) p = delta;
         else if (nneg == cnt) p = -delta;
@@ -385,8 +386,10 @@ inline int blocks_for(int total, int per_block, int cap) {
 }  // namespace
 
 int smem_max_layers(int width) {
-    // per warp: kTile columns x (lambda, T, W labels) floats per layer; at least one warp per block
-    return (200 * 1024) / (kTile * 4 * (2 + width));
+    // per warp: kTile columns x (lambda, T, W labels) floats per layer (staged kernels) or
+    // W labels per segment of kRegK layers (segmented kernels); at least one warp per block
+    if (width <= kRegW) return kRegK * ((200 * 1024 - kEpiMaxK * 2 * kTile * 4) / (kTile * 4 * width));
+    return (200 * 1024 - kEpiMaxK * 2 * kTile * 4) / (kTile * 4 * (2 + width));
 }
 
 cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
@@ -396,10 +399,13 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
         const bool reg = class_is_reg(cls);
         const int W = class_width(cls);
         int wpb = cfg.warps_per_block;
-        const int kstride = reg ? 0 : b.kmax[cls];
-        const int epi = ((mode == kFwdUpdate || mode == kBwdUpdate) && b.has_local[cls]) ? b.kmax[cls] : 0;
-        const size_t per_warp = (static_cast<size_t>(kstride) * (2 + W) + static_cast<size_t>(epi) * 2) * kTile *
-                                sizeof(float);
+        const bool seg = class_is_seg(cls);
+        // staged kernels: one row of state per layer; segmented kernels: one checkpoint per kRegK layers
+        const int kstride = reg ? 0 : (seg ? (b.kmax[cls] + kRegK - 1) / kRegK : b.kmax[cls]);
+        const int epi = ((mode == kFwdUpdate || mode == kBwdUpdate) && b.has_local[cls])
+                            ? (b.kmax[cls] < kEpiMaxK ? b.kmax[cls] : kEpiMaxK) : 0;
+        const size_t per_warp =
+            (static_cast<size_t>(kstride) * (seg ? W : 2 + W) + static_cast<size_t>(epi) * 2) * kTile * sizeof(float);
         while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
         const size_t smem = per_warp * wpb;
         SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags, epi};

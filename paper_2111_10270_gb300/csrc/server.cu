@@ -74,7 +74,7 @@ struct fdog_server {
 using namespace fdog;
 
 namespace fdog {
-int plan(fdog_instance* inst);
+int plan(fdog_instance* inst, bool compile_jit);
 size_t arena_size(const fdog_instance* inst);
 std::vector<int> jit_ids(const fdog_instance* inst);
 int release_device(fdog_instance* inst);
@@ -219,21 +219,28 @@ int fdog_server_submit(fdog_server* s, fdog_instance* inst, uint64_t* ticket) {
     if (!s || !inst || !ticket) return FDOG_EINVAL;
     if (inst->built) return FDOG_ESTATE;
     // host work in the caller's thread: planning and the specialised kernels
-    int rc = plan(inst);
+    int rc = plan(inst, false);
     if (rc != FDOG_OK) return rc;
-    std::vector<int> ids = jit_ids(inst);
+    std::vector<int> ids = jit_ids(inst), added;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->fatal != FDOG_OK) return s->fatal;
         for (int id : ids)
-            if (std::find(s->jit_universe.begin(), s->jit_universe.end(), id) == s->jit_universe.end())
+            if (std::find(s->jit_universe.begin(), s->jit_universe.end(), id) == s->jit_universe.end()) {
                 s->jit_universe.push_back(id);
+                added.push_back(id);
+            }
         ids = s->jit_universe;
     }
-    if (!ids.empty()) {
+    if (!added.empty()) {
+        // one module covers every shape submitted so far (cached per shape set,
+        // so a server that has seen these shapes before only loads it)
         std::string why;
-        rc = jit_compile(ids, why);  // cached per shape set; the worker then only loads it
+        rc = jit_compile(ids, why);
         if (rc != FDOG_OK) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            for (int id : added)
+                s->jit_universe.erase(std::find(s->jit_universe.begin(), s->jit_universe.end(), id));
             inst->last_error = why;
             return rc;
         }

@@ -324,6 +324,317 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     }
 }
 
+
+// Long rows (more than kRegK layers) of narrow BDDs (W <= kRegW).  Staging
+// every layer in shared memory would size each warp's region by the longest
+// row of the launch and starve the SM of warps, so the layers are processed
+// in segments of kRegK held in registers instead.  A first sweep over the
+// whole row keeps only the labels at segment starts (checkpoints, in shared
+// memory); the update sweep then visits the segments in its own direction,
+// reloads each one's multipliers and recomputes its labels from the next
+// checkpoint.  Every label and update is formed by the same operations in the
+// same order as in sweep_kernel, so results are identical; the cost is one
+// extra label sweep over data the warp has just read.
+// Shared memory per warp: a.kstride checkpoints x W labels x 32 lanes, then
+// the tile-local staging (a.epi layers).
+template <int W, int MODE>
+__global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
+    constexpr int C = kRegK;
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const size_t warp_floats = static_cast<size_t>(a.kstride) * W * kTile + static_cast<size_t>(a.epi) * kTile * 2;
+    float* wsm = smem + static_cast<size_t>(wib) * warp_floats;
+    float* cp = wsm + lane;  // checkpoint s, label v at cp[(s * W + v) * kTile]
+    float* ep_lam = wsm + static_cast<size_t>(a.kstride) * W * kTile;
+    int* ep_var = reinterpret_cast<int*>(ep_lam + static_cast<size_t>(a.epi) * kTile);
+    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        const int ii = find_inst(a.prefix, a.n_inst, g);
+        const InstDev* __restrict__ I = a.insts + ii;
+        if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
+            if (FDOG_INACTIVE(I->ctl)) continue;
+        }
+        const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
+        const ShapeDev sh = I->shapes[tile.shape];
+        const int k = sh.k;
+        const int nseg = (k + C - 1) / C;
+        const uint16_t* __restrict__ tpl = I->tpl + sh.tpl_off;
+        const bool valid = lane < tile.n_valid;
+        const float omega = I->omega;
+        const size_t base = static_cast<size_t>(tile.slot_base) + lane;
+        float* __restrict__ lam = I->lam;
+        constexpr bool update = MODE == kFwdUpdate || MODE == kBwdUpdate;
+        const bool need_t = update || (a.flags & kMMAddT);
+        const bool local = update && a.epi > 0 && tile.pattern >= 0;
+
+        // multiplier of layer t as sweep_kernel stages it (plus T in min-marginal
+        // and evaluation modes when asked), and the deferred term
+        auto load = [&](int t, float& l, float& tb) {
+            l = 0.f;
+            tb = 0.f;
+            if (valid) {
+                l = lam[base + static_cast<size_t>(t) * kTile];
+                if (need_t) tb = I->T[I->var[base + static_cast<size_t>(t) * kTile]];
+            }
+            if constexpr (MODE == kMinMarg || MODE == kEval) {
+                if (a.flags & kMMAddT) l += tb;
+            }
+        };
+
+        float term = 0.f;
+        if constexpr (MODE == kFwdUpdate || MODE == kMinMarg || MODE == kEval) {
+            // SP(v, TOP) over the whole row; keep the labels at segment starts
+            float nx[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) nx[v] = finf();
+#pragma unroll 4
+            for (int t = k - 1; t >= 0; --t) {
+                uint32_t c[W];
+                load_codes<W>(tpl + t * W, c);
+                float lt, tb;
+                load(t, lt, tb);
+                float cur[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) cur[v] = fminf(pick<W>(nx, c[v] & 0xFFu), pick<W>(nx, c[v] >> 8) + lt);
+#pragma unroll
+                for (int v = 0; v < W; ++v) nx[v] = cur[v];
+                if (t % C == 0) {
+#pragma unroll
+                    for (int v = 0; v < W; ++v) cp[((t / C) * W + v) * kTile] = cur[v];
+                }
+            }
+            if constexpr (MODE == kEval) term = nx[0];
+        }
+
+        if constexpr (MODE == kFwdUpdate || MODE == kMinMarg) {
+            float f[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) f[v] = v == 0 ? 0.f : finf();
+            float negsum = 0.f, E = finf();
+            float* __restrict__ mm0 = I->mm0;
+            float* __restrict__ mm1 = I->mm1;
+            for (int s = 0; s < nseg; ++s) {
+                const int t0 = s * C;
+                const int kk = (k - t0 < C) ? k - t0 : C;
+                float L[C], Tt[C], Sg[C][W], nxt[W];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    L[c] = 0.f;
+                    Tt[c] = 0.f;
+                    if (c < kk) {
+                        load(t0 + c, L[c], Tt[c]);
+                        if (local && valid) ep_var[(t0 + c) * kTile + lane] = I->var[base + static_cast<size_t>(t0 + c) * kTile];
+                    }
+                }
+                // labels of the segment's layers 1 .. kk-1, from the next checkpoint
+#pragma unroll
+                for (int v = 0; v < W; ++v) nxt[v] = (s + 1 < nseg) ? cp[((s + 1) * W + v) * kTile] : finf();
+                {
+                    float nx[W];
+#pragma unroll
+                    for (int v = 0; v < W; ++v) nx[v] = nxt[v];
+#pragma unroll
+                    for (int cc = C - 1; cc >= 1; --cc) {
+                        if (cc < kk) {
+                            uint32_t c[W];
+                            load_codes<W>(tpl + (t0 + cc) * W, c);
+                            float cur[W];
+#pragma unroll
+                            for (int v = 0; v < W; ++v)
+                                cur[v] = fminf(pick<W>(nx, c[v] & 0xFFu), pick<W>(nx, c[v] >> 8) + L[cc]);
+#pragma unroll
+                            for (int v = 0; v < W; ++v) { Sg[cc][v] = cur[v]; nx[v] = cur[v]; }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    if (c < kk) {
+                        const int t = t0 + c;
+                        uint32_t cd[W];
+                        load_codes<W>(tpl + t * W, cd);
+                        float b[W];
+#pragma unroll
+                        for (int v = 0; v < W; ++v) b[v] = (c + 1 < kk) ? Sg[(c + 1 < C) ? c + 1 : c][v] : nxt[v];
+                        float m0 = finf(), m1 = finf();
+#pragma unroll
+                        for (int v = 0; v < W; ++v) {
+                            m0 = fminf(m0, f[v] + pick<W>(b, cd[v] & 0xFFu));
+                            m1 = fminf(m1, f[v] + pick<W>(b, cd[v] >> 8));
+                        }
+                        const float lt = L[c];
+                        m1 += lt;
+                        float lt_new = lt;
+                        if constexpr (MODE == kFwdUpdate) {
+                            const float d = m1 - m0;
+                            lt_new = fmaf(-omega, d, lt) + Tt[c];  // Eq. 5
+                            L[c] = lt_new;
+                            negsum += fmaxf(-d, 0.f);
+                        } else {
+                            if (valid) {
+                                const size_t p = base + static_cast<size_t>(t) * kTile;
+                                if (a.flags & kMMBoth) { mm0[p] = m0; mm1[p] = m1; }
+                                else mm0[p] = m1 - m0;
+                            }
+                        }
+                        float nf[W];
+#pragma unroll
+                        for (int v = 0; v < W; ++v) nf[v] = finf();
+#pragma unroll
+                        for (int v = 0; v < W; ++v) {
+                            const uint32_t lo = cd[v] & 0xFFu, hi = cd[v] >> 8;
+                            push<W>(nf, lo, f[v]);
+                            push<W>(nf, hi, f[v] + lt_new);
+                            E = fminf(E, lo == kCodeTop ? f[v] : finf());
+                            E = fminf(E, hi == kCodeTop ? f[v] + lt_new : finf());
+                        }
+#pragma unroll
+                        for (int v = 0; v < W; ++v) f[v] = nf[v];
+                    }
+                }
+                if constexpr (MODE == kFwdUpdate) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        if (c < kk) {
+                            if (valid) lam[base + static_cast<size_t>(t0 + c) * kTile] = L[c];
+                            if (local) ep_lam[(t0 + c) * kTile + lane] = L[c];
+                        }
+                    }
+                }
+            }
+            term = fmaf(-omega, negsum, E);
+        }
+
+        if constexpr (MODE == kBwdUpdate) {
+            // SP(r, v) over the whole row; keep the labels at segment starts
+            {
+                float f[W];
+#pragma unroll
+                for (int v = 0; v < W; ++v) f[v] = v == 0 ? 0.f : finf();
+#pragma unroll 4
+                for (int t = 0; t < k; ++t) {
+                    uint32_t c[W];
+                    load_codes<W>(tpl + t * W, c);
+                    float lt, tb;
+                    load(t, lt, tb);
+                    if (t % C == 0) {
+#pragma unroll
+                        for (int v = 0; v < W; ++v) cp[((t / C) * W + v) * kTile] = f[v];
+                    }
+                    float nf[W];
+#pragma unroll
+                    for (int v = 0; v < W; ++v) nf[v] = finf();
+#pragma unroll
+                    for (int v = 0; v < W; ++v) {
+                        push<W>(nf, c[v] & 0xFFu, f[v]);
+                        push<W>(nf, c[v] >> 8, f[v] + lt);
+                    }
+#pragma unroll
+                    for (int v = 0; v < W; ++v) f[v] = nf[v];
+                }
+            }
+            float b[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) b[v] = finf();
+            float negsum = 0.f;
+            for (int s = nseg - 1; s >= 0; --s) {
+                const int t0 = s * C;
+                const int kk = (k - t0 < C) ? k - t0 : C;
+                float L[C], Tt[C], Sg[C][W];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    L[c] = 0.f;
+                    Tt[c] = 0.f;
+                    if (c < kk) {
+                        load(t0 + c, L[c], Tt[c]);
+                        if (local && valid) ep_var[(t0 + c) * kTile + lane] = I->var[base + static_cast<size_t>(t0 + c) * kTile];
+                    }
+                }
+                // labels of the segment's layers, from its checkpoint
+                {
+                    float f[W];
+#pragma unroll
+                    for (int v = 0; v < W; ++v) f[v] = cp[(s * W + v) * kTile];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        if (c < kk) {
+                            uint32_t cd[W];
+                            load_codes<W>(tpl + (t0 + c) * W, cd);
+                            float nf[W];
+#pragma unroll
+                            for (int v = 0; v < W; ++v) { Sg[c][v] = f[v]; nf[v] = finf(); }
+#pragma unroll
+                            for (int v = 0; v < W; ++v) {
+                                push<W>(nf, cd[v] & 0xFFu, f[v]);
+                                push<W>(nf, cd[v] >> 8, f[v] + L[c]);
+                            }
+#pragma unroll
+                            for (int v = 0; v < W; ++v) f[v] = nf[v];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int cc = C - 1; cc >= 0; --cc) {
+                    if (cc < kk) {
+                        uint32_t cd[W];
+                        load_codes<W>(tpl + (t0 + cc) * W, cd);
+                        float m0 = finf(), m1 = finf();
+#pragma unroll
+                        for (int v = 0; v < W; ++v) {
+                            const float fv = Sg[cc][v];
+                            m0 = fminf(m0, fv + pick<W>(b, cd[v] & 0xFFu));
+                            m1 = fminf(m1, fv + pick<W>(b, cd[v] >> 8));
+                        }
+                        const float lt = L[cc];
+                        m1 += lt;
+                        const float d = m1 - m0;
+                        const float lt_new = fmaf(-omega, d, lt) + Tt[cc];  // Eq. 5
+                        L[cc] = lt_new;
+                        negsum += fmaxf(-d, 0.f);
+                        float nb[W];
+#pragma unroll
+                        for (int v = 0; v < W; ++v)
+                            nb[v] = fminf(pick<W>(b, cd[v] & 0xFFu), pick<W>(b, cd[v] >> 8) + lt_new);
+#pragma unroll
+                        for (int v = 0; v < W; ++v) b[v] = nb[v];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    if (c < kk) {
+                        if (valid) lam[base + static_cast<size_t>(t0 + c) * kTile] = L[c];
+                        if (local) ep_lam[(t0 + c) * kTile + lane] = L[c];
+                    }
+                }
+            }
+            term = fmaf(-omega, negsum, b[0]);
+        }
+
+        if constexpr (update) {
+            if (local) {
+                __syncwarp();
+                tile_local_sums(I, tile.pattern, ep_lam, ep_var, lane);
+                __syncwarp();
+            }
+        }
+
+        float s = valid ? term : 0.f, comp = 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float o = __shfl_xor_sync(kFull, s, off);
+            const float oc = __shfl_xor_sync(kFull, comp, off);
+            const float sum = s + o;
+            const float bp = sum - s;
+            const float err = (s - (sum - bp)) + (o - bp);
+            s = sum;
+            comp = comp + oc + err;
+        }
+        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] =
+            static_cast<double>(s) + static_cast<double>(comp);
+    }
+}
+
 #undef FD_UP
 #undef FD_DOWN
 
@@ -344,6 +655,11 @@ cudaError_t launch_sweep_width(bool reg, int mode, int blocks, int threads, size
                : mode == kBwdUpdate ? dev::sweep_kernel<W, HAS_REG, kBwdUpdate>                                \
                : mode == kMinMarg   ? dev::sweep_kernel<W, HAS_REG, kMinMarg>                                  \
                                     : dev::sweep_kernel<W, HAS_REG, kEval>;                                    \
+        } else if (HAS_REG) {                                                                                  \
+            fn = mode == kFwdUpdate ? dev::sweep_seg_kernel<W, kFwdUpdate>                                     \
+               : mode == kBwdUpdate ? dev::sweep_seg_kernel<W, kBwdUpdate>                                     \
+               : mode == kMinMarg   ? dev::sweep_seg_kernel<W, kMinMarg>                                       \
+                                    : dev::sweep_seg_kernel<W, kEval>;                                         \
         } else {                                                                                               \
             fn = mode == kFwdUpdate ? dev::sweep_kernel<W, false, kFwdUpdate>                                  \
                : mode == kBwdUpdate ? dev::sweep_kernel<W, false, kBwdUpdate>                                  \

@@ -157,12 +157,21 @@ def test_wide_and_long_rows_plan(P, oracle_mod):
 
 def test_specialised_kernels_compile_on_the_host(P):
     """The shape-specialised kernels are generated and compiled with NVRTC
-    while planning (no GPU needed): every narrow short shape gets one."""
+    while planning (no GPU needed): with jit=1 every narrow short shape gets
+    one; in the default mode only shapes with at least 4096 BDDs do."""
     g = ilpgen.mrf_grid(8, 8, 3, 0)
-    inst = P.Instance.from_ilp(g)
+    inst = P.Instance.from_ilp(g, jit=1)
     inst.plan()
     kp = inst.kernel_plan()
     assert kp["note"] == "" and kp["jit_shapes"] == 2 and kp["static_tiles"] == 0
+    auto = P.Instance.from_ilp(g)
+    auto.plan()
+    assert auto.kernel_plan()["jit_shapes"] == 0
+    # 48 x 48 grid, 3 labels: 2304 simplex rows stay generic, 4512 x 6 marginalisation rows are specialised
+    big = P.Instance.from_ilp(ilpgen.mrf_grid(48, 48, 3, 0))
+    big.plan()
+    kb = big.kernel_plan()
+    assert kb["jit_shapes"] == 1 and kb["jit_tiles"] == 4512 * 6 // 32 and kb["static_tiles"] == 2304 // 32
     # the 8 marginalisation rows of an edge share its 9 pairwise variables; 4 edges per tile
     assert kp["local_vars"] > 0
     off = P.Instance.from_ilp(g, jit=-1)
@@ -171,7 +180,7 @@ def test_specialised_kernels_compile_on_the_host(P):
     assert kp["jit_shapes"] == 0 and kp["jit_tiles"] == 0 and kp["static_tiles"] > 0
     # random rows of many shapes, including ones too wide or long for the specialised code
     ilp = ilpgen.random_ilp(60, 50, 77, max_row=20, max_coef=2)
-    inst = P.Instance.from_ilp(ilp)
+    inst = P.Instance.from_ilp(ilp, jit=1)
     inst.plan()
     kp = inst.kernel_plan()
     assert kp["note"] == "" and kp["jit_shapes"] > 0

@@ -47,14 +47,15 @@ def solve_alone(P, ilp, max_iters, stream, **kw):
     return n, rounds, rc, x, obj, feas, lam
 
 
+@pytest.mark.parametrize("jit", [1, 0], ids=["specialised", "auto"])
 @pytest.mark.parametrize("use_stream", [False, True], ids=["default-stream", "graph-stream"])
-def test_batch_equals_solo(P, use_stream):
+def test_batch_equals_solo(P, use_stream, jit):
     import torch
 
     stream = torch.cuda.Stream() if use_stream else None
     ilps = mixed_instances()
-    alone = [solve_alone(P, g, 150, stream) for g in ilps]
-    insts = [P.Instance.from_ilp(g).build(0, stream) for g in ilps]
+    alone = [solve_alone(P, g, 150, stream, jit=jit) for g in ilps]
+    insts = [P.Instance.from_ilp(g, jit=jit).build(0, stream) for g in ilps]
     batch = P.Batch(insts, stream)
     iters, rounds, status = batch.solve(150)
     for q, (g, inst) in enumerate(zip(ilps, insts)):

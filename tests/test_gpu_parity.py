@@ -73,7 +73,7 @@ def test_fig2_first_iteration_matches_oracle_exactly(P, oracle_mod):
 # ----------------------------------------------------------------------------
 # trajectory and evaluation parity
 # ----------------------------------------------------------------------------
-def trajectory(P, oracle_mod, ilp, iters, omega=0.5, jit=0):
+def trajectory(P, oracle_mod, ilp, iters, omega=0.5, jit=1):
     """Same schedule on both sides; also returns the oracle's sum_j |E_j| after
     every iteration (the conditioning of the bound as a sum)."""
     inst = gpu_instance(P, ilp, omega=omega, jit=jit)
@@ -86,13 +86,13 @@ def trajectory(P, oracle_mod, ilp, iters, omega=0.5, jit=0):
     return inst, orc, gl, np.array(ol), np.array(cond)
 
 
-@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 @pytest.mark.parametrize("seed", range(3))
 def test_tiny_mrf_trajectory_parity(P, oracle_mod, seed, jit):
     g = ilpgen.mrf_grid(8, 8, 3, seed)
     inst, orc, gl, ol, _ = trajectory(P, oracle_mod, g, 200, jit=jit)
     kp = inst.kernel_plan()
-    assert (kp["static_tiles"] == 0) if jit == 0 else (kp["jit_tiles"] == 0), kp
+    assert (kp["static_tiles"] == 0) if jit == 1 else (kp["jit_tiles"] == 0), kp
     assert np.all(np.diff(gl) >= -1e-5 * max(1.0, abs(gl[-1])))
     bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t])]
     assert not bad, (bad[:5], gl[bad[0]], ol[bad[0]])
@@ -135,7 +135,7 @@ def test_tiny_mrf_evaluation_parity(P, oracle_mod, seed):
     assert np.abs(s - g.cost)[inb].max() <= 1e-5 * max(1.0, np.abs(g.cost).max())
 
 
-@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 @pytest.mark.parametrize("seed", range(8))
 def test_random_ilp_trajectory_parity(P, oracle_mod, seed, jit):
     ilp = ilpgen.random_ilp(40, 30, 700 + seed, max_row=9, max_coef=3)
@@ -150,7 +150,7 @@ def test_random_ilp_trajectory_parity(P, oracle_mod, seed, jit):
     assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
 
 
-@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 def test_wide_and_long_rows_parity(P, oracle_mod, jit):
     """Shapes of every kernel class: widths 2 / 4 / 8 / 16 with short and long
     rows, ragged tiles; with specialised kernels on, the narrow short shapes
@@ -177,7 +177,7 @@ def test_wide_and_long_rows_parity(P, oracle_mod, jit):
     inst = P.Instance.from_ilp(ilp, tol=0.0, jit=jit)
     inst.plan()
     kp = inst.kernel_plan()
-    assert kp["static_tiles"] > 0 and ((kp["jit_tiles"] > 0) == (jit == 0)), kp
+    assert kp["static_tiles"] > 0 and ((kp["jit_tiles"] > 0) == (jit == 1)), kp
     inst.build(0)
     orc = oracle_mod.Problem.from_ilp(ilp)
     gl = np.array([inst.iterate(1)[1] for _ in range(40)])
@@ -194,10 +194,64 @@ def test_wide_and_long_rows_parity(P, oracle_mod, jit):
     assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
 
 
+def long_narrow_rows(seed=6):
+    """Rows of width <= 4 and 9 .. 1000 layers: one-segment, multi-segment and
+    ragged-segment shapes of the segmented kernels, some shapes filling more
+    than one tile, some a tile with few BDDs."""
+    rng = np.random.default_rng(seed)
+    rb = ilpgen._RowBuilder()
+    n = 1500
+    kinds = [("le1", -1, 1), ("eq1", 0, 1), ("ge1", 1, 1), ("flow", -1, 0), ("le2", -1, 2), ("eq2", 0, 2),
+             ("le3", -1, 3)]
+    for k in (9, 12, 16, 17, 24, 40, 64, 65, 130, 300, 1000):
+        for q, (name, sense, rhs) in enumerate(kinds):
+            reps = 40 if (k == 17 and name == "le1") else (3 if k <= 65 else 1)
+            for _ in range(reps):
+                cols = np.sort(rng.choice(n, k, replace=False))
+                coef = [1] * k
+                if name == "flow":
+                    coef[0] = -1
+                rb.add(cols, coef, sense, rhs)
+    return rb.finish(n, rng.standard_normal(n), "long-narrow")
+
+
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
+def test_long_narrow_rows_parity(P, oracle_mod, jit):
+    """The segmented kernels (registers per segment of 8 layers, labels
+    recomputed from shared-memory checkpoints) against the oracle: bound
+    trajectory, min-marginals, and the evaluation of the finalised state."""
+    ilp = long_narrow_rows()
+    inst = P.Instance.from_ilp(ilp, tol=0.0, jit=jit)
+    inst.plan()
+    kp = inst.kernel_plan()
+    assert kp["static_tiles"] > 0, kp
+    inst.build(0)
+    orc = oracle_mod.Problem.from_ilp(ilp)
+    iters = 30
+    gl = np.array([inst.iterate(1)[1] for _ in range(iters)])
+    ol, cond = [], []
+    for _ in range(iters):
+        ol.append(orc.iterate(1)[0])
+        cond.append(np.abs(orc.energies()).sum())
+    bad = [t for t in range(iters) if not lb_close(gl[t], ol[t], scale=cond[t])]
+    assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    inst.finalize()
+    var, row, lam = inst.multipliers()
+    perm = slot_order(orc, var, row)
+    orc.set_state(lam[perm].astype(np.float64))
+    run, fea = inst.lower_bound()
+    _, ofea = orc.lower_bounds()
+    assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum())
+
+
 # ----------------------------------------------------------------------------
 # rounding
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 @pytest.mark.parametrize("seed", range(3))
 def test_tiny_mrf_rounding_parity(P, oracle_mod, seed, jit):
     g = ilpgen.mrf_grid(8, 8, 3, 20 + seed, potts_max=1.5)
@@ -273,7 +327,7 @@ def test_specialised_and_generic_kernels_agree(P, seed):
     generic kernels, so multipliers, bounds and min-marginals coincide."""
     g = ilpgen.mrf_grid(16, 16, 4, 40 + seed)
     out = []
-    for jit in (0, -1):
+    for jit in (1, -1):
         inst = gpu_instance(P, g, jit=jit)
         lbs = [inst.iterate(1)[1] for _ in range(15)]
         _, _, lam = inst.multipliers()
@@ -284,7 +338,7 @@ def test_specialised_and_generic_kernels_agree(P, seed):
     assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
 
 
-@pytest.mark.parametrize("jit", [0, -1], ids=["specialised", "generic"])
+@pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 def test_tile_local_sums_match_the_separate_pass(P, jit):
     """Deferred terms formed inside the sweep for tile-local variables use the
     same operations in the same order as the deferred-sum kernel: the whole

@@ -24,8 +24,8 @@ def P():
     return P
 
 
-def solo(P, g, max_iters):
-    inst = P.Instance.from_ilp(g).build(0)
+def solo(P, g, max_iters, jit=0):
+    inst = P.Instance.from_ilp(g, jit=jit).build(0)
     n, _ = inst.iterate(max_iters)
     rc, rounds = inst.primal_round()
     x, obj, feas = inst.solution()
@@ -38,12 +38,12 @@ def mix():
             ilpgen.fig2_example(), ilpgen.mrf_grid(20, 20, 2, 3)]
 
 
-@pytest.mark.parametrize("budget", [64 << 30, 1], ids=["roomy", "one-at-a-time"])
-def test_server_results_equal_solo(P, budget):
+@pytest.mark.parametrize("budget,jit", [(64 << 30, 1), (1, 0)], ids=["roomy-specialised", "one-at-a-time"])
+def test_server_results_equal_solo(P, budget, jit):
     ilps = mix()
-    ref = [solo(P, g, 200) for g in ilps]
+    ref = [solo(P, g, 200, jit) for g in ilps]
     srv = P.Server(0, hbm_budget=budget, max_active=64, max_iters=200)
-    tickets = [srv.submit(P.Instance.from_ilp(g)) for g in ilps]
+    tickets = [srv.submit(P.Instance.from_ilp(g, jit=jit)) for g in ilps]
     for t in tickets:
         assert srv.wait(t, 300)
     for g, t, (rc, rounds, x, obj, feas) in zip(ilps, tickets, ref):
@@ -79,3 +79,23 @@ def test_server_admits_while_busy(P):
         x, _, feas = srv.take(t).solution()
         assert feas and g.feasible(x)
     srv.close()
+
+
+def test_release_and_build_again(P):
+    """fdog_release frees the device memory; the solution stays readable and a
+    second build (same plan) solves to the same result."""
+    g = ilpgen.mrf_grid(12, 12, 3, 9)
+    inst = P.Instance.from_ilp(g).build(0)
+    inst.iterate(150)
+    inst.primal_round()
+    x, obj, feas = inst.solution()
+    inst.release()
+    x1, obj1, _ = inst.solution()
+    assert np.array_equal(x, x1) and obj == obj1
+    inst.release()  # nothing resident: still OK
+    inst.build(0)
+    inst.iterate(150)
+    inst.primal_round()
+    x2, obj2, feas2 = inst.solution()
+    assert np.array_equal(x, x2) and obj == obj2 and feas == feas2
+    inst.close()

@@ -74,10 +74,12 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *   seed = 0                   seed of the counter-based perturbation draws
  *   block_threads = 0          threads per CTA for the sweep kernels;
  *                              0 = use the built-in autotuner
- *   jit = 0                    shape-specialised sweep kernels, compiled at
- *                              build time with NVRTC for rows of width <= 4 and
- *                              length <= 16: 0 = use them when available
- *                              (falls back to the generic kernels), -1 = never
+ *   jit = 0                    shape-specialised sweep kernels, compiled with
+ *                              NVRTC for BDD shapes of width <= 4 and length
+ *                              <= 16: 0 = for such shapes with at least 4096
+ *                              BDDs in the instance, 1 = for every such shape,
+ *                              -1 = never; when NVRTC is unavailable the
+ *                              instance falls back to the generic kernels
  *   fuse = 0                   deferred sums of variables whose copies all lie
  *                              in one tile of 32 BDDs are formed inside the
  *                              update sweep (same operations, same order);
@@ -161,9 +163,19 @@ int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes,
  * lambda^j_i = c_i / |J_i| with M-bar = 0 (Alg. 1 text).
  * Errors: FDOG_EINFEASIBLE (a row cannot be satisfied), FDOG_ENOMEM (host or
  * device memory, or a row whose BDD exceeds the node limit), FDOG_ECUDA,
- * FDOG_ESTATE if already built.  May be called once per instance.
+ * FDOG_ESTATE if already built.  After fdog_release the instance may be
+ * built again (on any device and stream); its plan is reused.
  */
 int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream);
+
+/*
+ * Free the instance's device memory (no counterpart in the paper: memory
+ * management for callers that keep many instances).  The plan, the last
+ * rounded solution and its objective stay readable on the host; the dual
+ * state is dropped.  Waits for the instance's stream first.  FDOG_OK also
+ * when nothing is resident.
+ */
+int fdog_release(fdog_instance* inst);
 
 /*
  * Re-initialise the dual state on the device: lambda^j_i = c_i / |J_i|,
@@ -224,9 +236,12 @@ int fdog_multipliers(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_
  * Perturbation primal rounding (Alg. 2): add the pending deferred
  * differences back, compute all M_ij, and while some variable's M_ij do not
  * all share one strict sign, perturb every variable by the four cases of
- * Alg. 2 (r uniform in [-1, 1) from SplitMix64(seed ^ round<<32 ^ i)), grow
- * delta by alpha, re-run rounding_dual_iters iterations of Alg. 1 and the
- * add-back, and recompute M.  At agreement x_i = [M_ij < 0].
+ * Alg. 2: +delta / -delta where all M_ij are positive / negative, r * delta
+ * where all are zero, sign(sum_j M_ij) |r| delta otherwise, with r uniform in
+ * [-delta, delta) from u = SplitMix64(seed ^ round<<32 ^ i) as
+ * r = delta (2u - 1); then grow delta by alpha, re-run rounding_dual_iters
+ * iterations of Alg. 1 and the add-back, and recompute M.  At agreement
+ * x_i = [M_ij < 0].
  * *rounds_used (may be NULL) receives the number of perturbation rounds.
  * Returns FDOG_ENOCONVERGE after max_rounds rounds without agreement (the
  * solution is then x_i = [sum_j M_ij < 0], possibly infeasible).

@@ -6,7 +6,8 @@
  * Discrete Optimization on GPU", CVPR 2022):
  *
  *   - BDD construction for one linear row a^T x in [L, U]      (Def. 4, Ex. 1)
- *   - presolve of forced variables / always-true rows           (reading O13)
+ *   - presolve of forced variables / always-true rows           (a forced variable
+ *     would give infinite min-marginal differences, so it is fixed first)
  *   - shortest paths and min-marginals on a weighted BDD        (Eq. 6, Alg. 3, Alg. 4)
  *   - parallel deferred min-marginal averaging, lifted form     (Alg. 1, Eq. 5, Prop. 1 proof)
  *   - the final deferred add-back                               (Alg. 1, last loop)
@@ -23,11 +24,10 @@
  *   - The dual state is kept in the lifted representation of the Appendix
  *     (a pair hi = lambda^{j,1}_i, lo = lambda^{j,0}_i per slot); the plain
  *     multiplier is lambda = hi - lo.
- *   - Readings of ambiguous passages follow the list in the design notes:
- *     M-bar is refreshed after every pass (O1); the final step adds the
- *     averaged deferred differences (O2); the lifted update subtracts the
- *     positive parts and adds their averages (O3); arcs leaving layer i carry
- *     lambda_i (O4, pinned by Fig. 3).
+ *   - Where the paper leaves a detail open: M-bar is refreshed after every
+ *     pass; the final step of Alg. 1 adds the averaged deferred differences
+ *     back; the lifted update subtracts the positive parts and adds their
+ *     averages; arcs leaving layer i carry lambda_i (pinned by Fig. 3).
  *
  * Status codes: 0 ok, -1 invalid input, -2 out of memory / too large,
  * -3 infeasible, -5 wrong call order, -7 rounding did not converge.
@@ -262,7 +262,7 @@ typedef struct {
 
 static double pos(double x) { return x > 0 ? x : 0; }
 
-/* presolve (reading O13): repeatedly substitute fixed variables into rows,
+/* presolve: repeatedly substitute fixed variables into rows,
    drop rows whose feasible set is the full cube, fix variables that a row
    forces, until nothing changes. */
 static int presolve_and_build(orc_problem *p, int n_rows, const int64_t *row_ptr, const int32_t *col,
@@ -411,7 +411,7 @@ int orc_create(int n_vars, const double *cost, int n_rows, const int64_t *row_pt
             p->const_lb += p->c[i] * p->fixed[i];
             p->const_obj_fixed += p->c[i] * p->fixed[i];
         } else if (p->cnt[i] == 0) {
-            p->fixed[i] = 2; /* in no row: x_i = [c_i < 0] (reading O12) */
+            p->fixed[i] = 2; /* in no row: x_i = [c_i < 0], bound += min(c_i, 0) */
             p->const_lb += p->c[i] < 0 ? p->c[i] : 0;
         }
     }
@@ -502,11 +502,11 @@ static void refresh_spf(orc_problem *p) {
  * previous pass).  forward = 1: layers in ascending order, shortest paths from
  * the root updated incrementally (Alg. 3) against SP(., TOP) of the previous
  * backward pass; forward = 0: descending order (Alg. 4) against SP(r, .) of
- * the previous forward pass.  Per slot (Eq. 5 in lifted form, reading O3):
+ * the previous forward pass.  Per slot (Eq. 5 in lifted form):
  *     d = m^1 - m^0
  *     hi -= omega * max(d, 0);        lo -= omega * max(-d, 0)
  *     hi += omega * Dbar1_i / |J_i|;  lo += omega * Dbar0_i / |J_i|
- * and D^beta_i accumulates max(+-d, 0).  After the pass M-bar <- M (O1).
+ * and D^beta_i accumulates max(+-d, 0).  After the pass M-bar <- M.
  * M_out (may be NULL) receives d per slot.
  */
 static void run_pass(orc_problem *p, int forward, double omega, double *M_out) {
@@ -577,7 +577,7 @@ static int64_t max_layers(const orc_problem *p) {
 
 /* lower bounds at the current state (nothing is modified):
    running  = sum_j E(hi^j, lo^j) + constant          (lifted bound, Prop. 1 proof)
-   feasible = the same after the final add-back of Alg. 1 (reading O2). */
+   feasible = the same after the final add-back of Alg. 1. */
 int orc_lower_bounds(const orc_problem *p, double omega, double *lb_running, double *lb_feasible) {
     double *scr = malloc(sizeof(double) * max_nodes(p));
     int64_t K = max_layers(p);
@@ -631,7 +631,7 @@ int orc_iterate(orc_problem *p, int k, double omega, double *lb_trace) {
     return ORC_OK;
 }
 
-/* final step of Alg. 1: add the deferred differences back (averaged, O2) */
+/* final step of Alg. 1: add the deferred differences back (averaged) */
 int orc_addback(orc_problem *p, double omega) {
     for (int64_t s = 0; s < p->S; ++s) {
         int i = p->svar[s];
@@ -676,7 +676,8 @@ static uint64_t splitmix64(uint64_t x) {
 
 uint64_t orc_splitmix64(uint64_t x) { return splitmix64(x); }
 
-/* r uniform in [-1, 1) for (seed, round, variable): reading O19 */
+/* u uniform in [0, 1) from SplitMix64(seed ^ round << 32 ^ variable), returned
+   as 2u - 1 in [-1, 1); Alg. 2 scales it by delta to draw r from [-delta, delta) */
 double orc_uniform_pm1(uint64_t seed, int round, int var) {
     uint64_t h = splitmix64(seed ^ ((uint64_t)(uint32_t)round << 32) ^ (uint64_t)(uint32_t)var);
     double u = (double)(h >> 11) * (1.0 / 9007199254740992.0);
@@ -685,11 +686,13 @@ double orc_uniform_pm1(uint64_t seed, int round, int var) {
 
 /*
  * Alg. 2.  Starts with the final add-back of Alg. 1, computes all M_ij, and
- * while some variable's differences do not all share one strict sign (reading
- * O16), perturbs every variable (cases of Alg. 2; r from reading O19; the
- * zero-sum conflict case uses sign(r), O15), multiplies delta by alpha,
- * re-optimises with `kr` iterations of Alg. 1 from M-bar = 0 followed by the
- * add-back (reading O17), and recomputes M.  At agreement x_i = [M_ij < 0].
+ * while some variable's differences do not all share one strict nonzero sign
+ * (all-zero differences count as disagreement: they fix no assignment),
+ * perturbs every variable by the cases of Alg. 2 with r uniform in
+ * [-delta, delta) (the conflict case with sum_j M_ij = 0 takes sign(r)),
+ * multiplies delta by alpha, re-optimises with `kr` iterations of Alg. 1 from
+ * M-bar = 0 followed by the add-back, and recomputes M.  At agreement
+ * x_i = [M_ij < 0].
  * Output: x (n bytes), rounds used, objective c^T x, and `margin` = the smallest
  * |M_ij| (and |sum_j M_ij| of conflicting variables) met in any round's
  * decisions, which bounds how robust the decisions are to rounding error.
@@ -733,7 +736,8 @@ int orc_round(orc_problem *p, double omega, double delta, double alpha, int kr, 
                 npos += v > 0; nneg += v < 0; nzero += v == 0;
                 sum += v;
             }
-            double r = orc_uniform_pm1(seed, round, i);
+            /* Alg. 2 draws r uniformly from [-delta, delta] and pushes by r * delta */
+            double r = orc_uniform_pm1(seed, round, i) * delta;
             double pert;
             if (npos == c) pert = delta;
             else if (nneg == c) pert = -delta;

@@ -417,6 +417,65 @@ def test_rounding_returns_feasible_point_above_bound(oracle_mod, seed):
         assert r["status"] == oracle_mod.ENOCONVERGE
 
 
+def _two_var_rounding_rounds(oracle_mod, seed, alpha=1.2):
+    """Expected multipliers after two rounds of Alg. 2 on x0 + x1 <= 1 and
+    x0 + x1 >= 1 with zero costs and no re-optimisation, worked out from the
+    closed-form min-marginals of two-variable rows (lambda^j_i = p_i in both):
+      x0 + x1 <= 1:  m1(x0) = p0,              m0(x0) = min(0, p1)
+      x0 + x1 >= 1:  m1(x0) = p0 + min(0, p1), m0(x0) = p1
+    Round 0 sees M = 0 everywhere (zero costs), so each variable moves by
+    r delta with r drawn from [-delta, delta), delta = 1.  Round 1 has
+    delta = alpha."""
+    u = lambda rnd, i: oracle_mod.uniform_pm1(seed, rnd, i)
+    p = [u(0, 0) * 1.0 * 1.0, u(0, 1) * 1.0 * 1.0]
+    d1 = alpha
+    q, conflict = [], []
+    for i in (0, 1):
+        a, b = p[i], p[1 - i]
+        m_le = a - min(0.0, b)
+        m_ge = a + min(0.0, b) - b
+        ms = [m_le, m_ge]
+        r = u(1, i) * d1
+        if all(m > 0 for m in ms):
+            q.append(d1); conflict.append(False)
+        elif all(m < 0 for m in ms):
+            q.append(-d1); conflict.append(False)
+        elif all(m == 0 for m in ms):
+            q.append(r * d1); conflict.append(False)
+        else:
+            tot = m_le + m_ge
+            sg = 1.0 if tot > 0 else (-1.0 if tot < 0 else (1.0 if r >= 0 else -1.0))
+            q.append(sg * abs(r) * d1); conflict.append(True)
+    return p, q, conflict
+
+
+def test_rounding_perturbation_worked_example(oracle_mod):
+    """The perturbation step of Alg. 2, two rounds, with r drawn from
+    [-delta, delta) and pushed as r delta: a conflicting variable in round 1
+    moves by up to alpha^2 = 1.44 (a draw from [-1, 1) would give at most
+    1.2).  Seeds are scanned for one whose round 1 has a conflict."""
+    rb = ilpgen._RowBuilder()
+    rb.add([0, 1], [1, 1], -1, 1)
+    rb.add([0, 1], [1, 1], 1, 1)
+    ilp = rb.finish(2, np.zeros(2), "two-var")
+    checked = 0
+    for seed in range(64):
+        p, q, conflict = _two_var_rounding_rounds(oracle_mod, seed)
+        if not any(conflict):
+            continue
+        prob = oracle_mod.Problem.from_ilp(ilp)
+        prob.round(omega=0.5, delta=1.0, alpha=1.2, kr=0, max_rounds=2, seed=seed)
+        hi, lo, _, _ = prob.state()
+        lam = hi - lo
+        var = prob.slot_vars()
+        want = np.array([p[v] + q[v] for v in var])
+        assert np.allclose(lam, want, rtol=0, atol=1e-12), (seed, lam, want)
+        checked += 1
+        if any(c and abs(q[i]) > 1.2 for i, c in enumerate(conflict)):
+            break
+    assert checked > 0 and any(c and abs(q[i]) > 1.2 for i, c in enumerate(conflict))
+
+
 def test_tiny_mrf_sizes_and_rounding(oracle_mod):
     g = ilpgen.mrf_grid(8, 8, 3, 0)
     p = oracle_mod.Problem.from_ilp(g)

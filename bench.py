@@ -465,9 +465,9 @@ def main():
     # per sweep launch: per slot lambda read + write, variable id, deferred-term gather (16 B); per tile its
     # descriptor and bound partial (40 B); per tile-local variable its target C and new deferred term (8 B)
     alg_bytes = 16 * S + 40 * tiles + 8 * kp["local_vars"]
-    # per deferred-sum launch: per listed variable its id, record, C and T (20 B); per copy the gathered
-    # multiplier (4 B), plus the overflow list entries of variables with more than two copies
-    reduce_bytes = 20 * kp["work_vars"] + 4 * kp["work_slots"] + 4 * max(kp["work_slots"] - 2 * kp["work_vars"], 0)
+    # per deferred-sum launch: per listed variable its id, C and the new T (12 B); per copy its slot
+    # position and the gathered multiplier (8 B)
+    reduce_bytes = 12 * kp["work_vars"] + 8 * kp["work_slots"]
     sweep_avg_s = prof["sweep_ms"] / max(prof["sweep_launches"], 1) / 1e3
     reduce_avg_s = prof["reduce_ms"] / max(prof["reduce_launches"], 1) / 1e3
     achieved = alg_bytes / sweep_avg_s / 1e9 if sweep_avg_s > 0 else None

@@ -80,7 +80,8 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.patterns), sizeof(int32_t) * std::max<size_t>(d.patterns.size(), 2)},
         {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * std::max<size_t>(d.local_ent.size(), 4)},
         {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * std::max<size_t>(d.work.size(), 1)},
-        {reinterpret_cast<void**>(&a.tile_lb), sizeof(double) * sz(nt)},
+        {reinterpret_cast<void**>(&a.wpos), sizeof(int32_t) * std::max<size_t>(d.wpos.size(), 1)},
+        {reinterpret_cast<void**>(&a.tile_lb), sizeof(float2) * sz(nt)},
         {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
         {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
         {reinterpret_cast<void**>(&a.prefix), sizeof(int32_t) * kPrefixInts},
@@ -177,7 +178,10 @@ int allocate_and_upload(fdog_instance* inst) {
     h.patterns = a.patterns;
     h.local_ent = a.local_ent;
     h.work = a.work;
+    h.wpos = a.wpos;
     h.n_work = static_cast<int32_t>(d.work.size());
+    for (int b = 0; b <= FDOG_WBUCKETS; ++b) h.wb_start[b] = d.wb_start[b];
+    for (int b = 0; b < FDOG_WBUCKETS; ++b) h.wb_pos[b] = d.wb_pos[b];
     h.cost = a.cost;
     h.pert = a.pert;
     h.x = a.x;
@@ -252,6 +256,7 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.patterns, d.patterns.data(), sizeof(int32_t) * d.patterns.size());
     up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
     up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());
+    up(a.wpos, d.wpos.data(), sizeof(int32_t) * d.wpos.size());
     up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
     if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
     return FDOG_OK;
@@ -624,9 +629,21 @@ int fdog_dual_iterate(fdog_instance* inst, int32_t k, int32_t* iters_done, doubl
         Engine* e;
         BatchView* v;
         if ((rc = own_engine(inst, &e, &v)) != FDOG_OK) return rc;
-        // the instance runs exactly k iterations unless its stopping rule fires first
+        // the instance runs exactly k iterations unless its stopping rule fires
+        // first; with the rule on, the status is polled every two graph chunks
+        // so that launches stop soon after the device stops iterating
         rc = view_op(*e, *v, kOpLimit, k);
-        if (rc == FDOG_OK) rc = view_iterate(*e, *v, k);
+        const int poll = before.stop_enabled ? 2 * std::max(e->chunk, 1) : k;
+        for (int left = k; rc == FDOG_OK && left > 0;) {
+            const int step = std::min(left, poll);
+            rc = view_iterate(*e, *v, step);
+            left -= step;
+            if (rc == FDOG_OK && left > 0) {
+                std::vector<InstStatus> st;
+                rc = view_status(*e, *v, st);
+                if (rc == FDOG_OK && (st[0].done || st[0].iter >= st[0].iter_limit)) break;
+            }
+        }
         if (rc != FDOG_OK) {
             inst->last_error = e->err;
             return rc;

@@ -408,16 +408,32 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
                     out.cls_has_local[c] = true;
         }
     }
+    // The other variables go to the deferred-sum kernel, bucketed by copy
+    // count so that a warp reads its variables' slot positions column by
+    // column (coalesced); more than FDOG_WBUCKETS - 1 copies: the last bucket.
+    std::vector<std::vector<int32_t>> bucket(FDOG_WBUCKETS);
     for (int32_t i = 0; i < n_vars; ++i) {
         const int32_t c = out.csr_off[i + 1] - out.csr_off[i];
         if (local[i]) {
             ++out.n_local_vars;
         } else if (c > 0) {
-            out.work.push_back(i);
+            bucket[std::min(c, FDOG_WBUCKETS) - 1].push_back(i);
             out.n_work_slots += c;
-            if (c > 2) out.n_work_overflow += c;
+            if (c >= FDOG_WBUCKETS) out.n_work_overflow += c;
         }
     }
+    for (int b = 0; b < FDOG_WBUCKETS; ++b) {
+        out.wb_start[b] = static_cast<int32_t>(out.work.size());
+        out.wb_pos[b] = static_cast<int32_t>(out.wpos.size());
+        out.work.insert(out.work.end(), bucket[b].begin(), bucket[b].end());
+        if (b == FDOG_WBUCKETS - 1) continue;
+        const size_t nb = bucket[b].size();
+        out.wpos.resize(out.wpos.size() + (b + 1) * nb);
+        for (int q = 0; q <= b; ++q)
+            for (size_t j = 0; j < nb; ++j)
+                out.wpos[out.wb_pos[b] + q * nb + j] = out.csr_pos[out.csr_off[bucket[b][j]] + q];
+    }
+    out.wb_start[FDOG_WBUCKETS] = static_cast<int32_t>(out.work.size());
     return FDOG_OK;
 }
 

@@ -1,6 +1,8 @@
 // Internal types shared by the host-side builder and the CUDA kernels.
 #pragma once
 
+#include <vector_types.h>  // float2 in the device descriptors
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -97,6 +99,10 @@ struct InstCtl {
 #define FDOG_INACTIVE(ctl) ((ctl)->done || (ctl)->iter >= (ctl)->iter_limit)
 
 // Everything a kernel needs to know about one instance (device pointers).
+// deferred-sum work buckets: copy counts 1 .. FDOG_WBUCKETS - 1, then one
+// bucket for variables with more copies (read through vrec / csr_pos)
+#define FDOG_WBUCKETS 9
+
 struct InstDev {
     const TileDev* tiles;
     const ShapeDev* shapes;
@@ -113,11 +119,14 @@ struct InstDev {
                              //       a < 0: |J_i| = b copies listed at csr_pos[-a - 1 ...]
     const int32_t* patterns; // [2 per pattern] {first entry, entries}: variables whose copies all lie in one tile
     const uint16_t* local_ent;  // [4 per entry] copy offsets (32 t + lane) within the tile, ascending, 0xFFFF unused
-    const int32_t* work;     // [n_work] variables the deferred-sum kernel handles (copies in several tiles)
+    const int32_t* work;     // [n_work] variables the deferred-sum kernel handles (copies in several tiles),
+                             //          grouped into buckets by copy count (FDOG_WBUCKETS)
+    const int32_t* wpos;     // slot positions of the bucketed variables: bucket b (count c = b + 1, nb
+                             // variables) holds copy q of its j-th variable at wpos[wb_pos[b] + q nb + j]
     const double* cost;      // [n]
     float* pert;             // [n] rounding perturbation of this round
     uint8_t* x;              // [n] rounded solution
-    double* tile_lb;         // [n_tiles] per-tile partial of the lower bound
+    float2* tile_lb;         // [n_tiles] per-tile partial of the lower bound: compensated pair (sum, error)
     double* chunk_lb;        // [n_chunks] per-chunk partials of the lower-bound reduction
     double* obj_chunk;       // [n_obj_chunks]
     InstCtl* ctl;
@@ -126,6 +135,8 @@ struct InstDev {
     int32_t n_chunks;
     int32_t n_obj_chunks;
     int32_t n_work;
+    int32_t wb_start[FDOG_WBUCKETS + 1];  // first work index of each bucket; [FDOG_WBUCKETS] = n_work
+    int32_t wb_pos[FDOG_WBUCKETS];        // offset of each bucket's columns in wpos
     float omega;
     double const_lb;
     double alpha;            // rounding: perturbation growth
@@ -182,7 +193,10 @@ struct Decomposition {
     std::vector<int32_t> vrec;     // 2 ints per variable (see InstDev::vrec)
     std::vector<int32_t> patterns;  // 2 ints per pattern (see InstDev::patterns)
     std::vector<uint16_t> local_ent;
-    std::vector<int32_t> work;      // variables left to the deferred-sum kernel
+    std::vector<int32_t> work;      // variables left to the deferred-sum kernel, bucketed by copy count
+    std::vector<int32_t> wpos;      // bucketed slot positions (see InstDev::wpos)
+    int32_t wb_start[FDOG_WBUCKETS + 1] = {0};
+    int32_t wb_pos[FDOG_WBUCKETS] = {0};
     int64_t n_local_vars = 0;
     int64_t n_work_slots = 0;       // copies of the variables in `work`
     int64_t n_work_overflow = 0;    // of those, list entries read from csr_pos (variables with > 2 copies)

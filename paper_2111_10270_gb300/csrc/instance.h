@@ -38,7 +38,8 @@ struct DevArrays {
     int32_t* patterns = nullptr;
     uint16_t* local_ent = nullptr;
     int32_t* work = nullptr;
-    double* tile_lb = nullptr;
+    int32_t* wpos = nullptr;
+    float2* tile_lb = nullptr;
     double* chunk_lb = nullptr;
     double* obj_chunk = nullptr;
     int32_t* prefix = nullptr;

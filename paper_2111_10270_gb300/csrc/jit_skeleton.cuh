@@ -77,7 +77,7 @@ __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
             s = sum;
             comp = comp + oc + err;
         }
-        if (lane == 0) I->tile_lb[ti] = (double)s + (double)comp;
+        if (lane == 0) I->tile_lb[ti] = make_float2(s, comp);
     }
 }
 

@@ -45,20 +45,28 @@ __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     if (FDOG_INACTIVE(I->ctl)) return;
-    const int i = I->work[g - __ldg(a.prefix + ii)];  // variables with copies in several tiles
-    const int2 r = reinterpret_cast<const int2*>(I->vrec)[i];
+    const int w = g - __ldg(a.prefix + ii);
+    const int i = I->work[w];  // a variable with copies in several tiles
+    int b = 0;
+#pragma unroll
+    for (int q = 1; q < FDOG_WBUCKETS; ++q) b += w >= I->wb_start[q];
     const float* __restrict__ lam = I->lam;
-    float s = 0.f;
+    float s = 0.f;  // copies in ascending slot order, as in csr_pos: a fixed summation order
     int cnt;
-    if (r.x >= 0) {
-        const float l0 = lam[r.x];
-        const float l1 = r.y >= 0 ? lam[r.y] : 0.f;
-        s += l0;  // ascending slot order, as in csr_pos: a fixed summation order
-        if (r.y >= 0) s += l1;
-        cnt = r.y >= 0 ? 2 : 1;
+    if (b < FDOG_WBUCKETS - 1) {
+        // bucket of b + 1 copies: positions column by column, all loads independent
+        cnt = b + 1;
+        const int nb = I->wb_start[b + 1] - I->wb_start[b];
+        const int32_t* __restrict__ pos = I->wpos + I->wb_pos[b] + (w - I->wb_start[b]);
+        float l[FDOG_WBUCKETS - 1];
+#pragma unroll
+        for (int q = 0; q < FDOG_WBUCKETS - 1; ++q) l[q] = q < cnt ? lam[pos[q * nb]] : 0.f;
+#pragma unroll
+        for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
+            if (q < cnt) s += l[q];
     } else {
+        const int2 r = reinterpret_cast<const int2*>(I->vrec)[i];
         cnt = r.y;
-        if (cnt == 0) return;
         const int32_t* __restrict__ pos = I->csr_pos + (-r.x - 1);
         for (int p = 0; p < cnt; ++p) s += lam[pos[p]];
     }
@@ -82,6 +90,40 @@ struct LbArgs {
 __device__ __forceinline__ void neumaier_pair(double& s, double& c, double x, double y) {
     neumaier(s, c, x);
     c += y;
+}
+
+// (s, c) <- (s, c) + (x, y) for compensated FP32 pairs (TwoSum of the sums)
+__device__ __forceinline__ void pair_add_f(float& s, float& c, float x, float y) {
+    const float t = s + x;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (x - bp);
+    s = t;
+    c = c + y + e;
+}
+
+// the same fixed-order block reduction for compensated FP32 pairs
+__device__ __forceinline__ void block_pair_reduce_f(float* ss, float* sc, float& s, float& c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, s, off);
+        const float oc = __shfl_xor_sync(0xffffffffu, c, off);
+        pair_add_f(s, c, os, oc);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        sc[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < 8 ? ss[threadIdx.x] : 0.f;
+        c = threadIdx.x < 8 ? sc[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, s, off);
+            const float oc = __shfl_xor_sync(0xffffffffu, c, off);
+            pair_add_f(s, c, os, oc);
+        }
+    }
 }
 
 // block-wide fixed-order reduction of one Neumaier pair per thread
@@ -116,6 +158,7 @@ __device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double
 // on the instance, so its bound is the same alone or in a batch.
 __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     __shared__ double ss[8], sc[8];
+    __shared__ float ssf[8], scf[8];
     __shared__ int last;
     const int g = blockIdx.x;
     const int ii = find_inst(a.prefix, a.n_inst, g);
@@ -124,20 +167,20 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     if (a.target == kLbIterate && FDOG_INACTIVE(ctl)) return;
     const int c = g - __ldg(a.prefix + ii);
     const int t = c * kLbChunk + threadIdx.x;
-    double s = t < I->n_tiles ? I->tile_lb[t] : 0.0, cp = 0.0;
-    block_pair_reduce(ss, sc, s, cp);
+    // the chunk's tile partials as compensated FP32 pairs (FP64 is a small
+    // fraction of the FP32 rate here); the pair is exact in FP64 afterwards
+    float2 p = t < I->n_tiles ? I->tile_lb[t] : make_float2(0.f, 0.f);
+    block_pair_reduce_f(ssf, scf, p.x, p.y);
     if (threadIdx.x == 0) {
-        I->chunk_lb[c] = s + cp;
+        I->chunk_lb[c] = static_cast<double>(p.x) + static_cast<double>(p.y);
         __threadfence();
         last = atomicAdd(&ctl->ticket, 1) == I->n_chunks - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    s = 0.0;
-    cp = 0.0;
+    double s = 0.0, cp = 0.0;
     for (int q = threadIdx.x; q < I->n_chunks; q += blockDim.x) neumaier(s, cp, __ldcg(I->chunk_lb + q));
-    __syncthreads();  // the shared partials of the first reduction are reused
     block_pair_reduce(ss, sc, s, cp);
     if (threadIdx.x == 0) {
         double S = s, Cc = cp;
@@ -322,17 +365,34 @@ __global__ void __launch_bounds__(256) objective_kernel(LbArgs a) {
         }
         __syncthreads();
     }
+    __shared__ int last;
     if (threadIdx.x == 0) {
         I->obj_chunk[c] = ss[0] + sc[0];
         __threadfence();
-        const int ticket = atomicAdd(&ctl->obj_ticket, 1);
-        if (ticket == I->n_obj_chunks - 1) {
-            __threadfence();
-            double S = 0.0, Cc = 0.0;
-            for (int q = 0; q < I->n_obj_chunks; ++q) neumaier(S, Cc, __ldcg(I->obj_chunk + q));
-            ctl->objective = S + Cc;
-            ctl->obj_ticket = 0;
+        last = atomicAdd(&ctl->obj_ticket, 1) == I->n_obj_chunks - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block sums the chunk totals, strided over its threads then a fixed-order tree
+    __threadfence();
+    s = 0.0;
+    cp = 0.0;
+    for (int q = threadIdx.x; q < I->n_obj_chunks; q += blockDim.x) neumaier(s, cp, __ldcg(I->obj_chunk + q));
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = cp;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double x = ss[threadIdx.x], y = ss[threadIdx.x + w], cc = sc[threadIdx.x] + sc[threadIdx.x + w];
+            neumaier(x, cc, y);
+            ss[threadIdx.x] = x;
+            sc[threadIdx.x] = cc;
         }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctl->objective = ss[0] + sc[0];
+        ctl->obj_ticket = 0;
     }
 }
 

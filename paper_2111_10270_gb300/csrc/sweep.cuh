@@ -319,8 +319,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             s = sum;
             comp = comp + oc + err;
         }
-        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] =
-            static_cast<double>(s) + static_cast<double>(comp);
+        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
     }
 }
 
@@ -630,8 +629,7 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
             s = sum;
             comp = comp + oc + err;
         }
-        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] =
-            static_cast<double>(s) + static_cast<double>(comp);
+        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
     }
 }
 

@@ -76,7 +76,6 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.cost), sizeof(double) * sz(n)},
         {reinterpret_cast<void**>(&a.csr_off), sizeof(int32_t) * static_cast<size_t>(n + 1)},
         {reinterpret_cast<void**>(&a.csr_pos), sizeof(int32_t) * sz(d.n_slots)},
-        {reinterpret_cast<void**>(&a.vrec), 2 * sizeof(int32_t) * sz(n)},
         {reinterpret_cast<void**>(&a.patterns), sizeof(int32_t) * std::max<size_t>(d.patterns.size(), 2)},
         {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * std::max<size_t>(d.local_ent.size(), 4)},
         {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * std::max<size_t>(d.work.size(), 1)},
@@ -174,7 +173,6 @@ int allocate_and_upload(fdog_instance* inst) {
     h.C = a.C;
     h.csr_off = a.csr_off;
     h.csr_pos = a.csr_pos;
-    h.vrec = a.vrec;
     h.patterns = a.patterns;
     h.local_ent = a.local_ent;
     h.work = a.work;
@@ -230,8 +228,10 @@ int allocate_and_upload(fdog_instance* inst) {
     b.vars_total = static_cast<int32_t>(n);
     two(&b.tile_all_prefix, static_cast<int32_t>(nt));
     b.tiles_all_total = static_cast<int32_t>(nt);
-    two(&b.work_prefix, static_cast<int32_t>(d.work.size()));
-    b.work_total = static_cast<int32_t>(d.work.size());
+    two(&b.work_prefix, d.wb_start[FDOG_WBUCKETS - 1]);
+    b.work_total = d.wb_start[FDOG_WBUCKETS - 1];
+    two(&b.wide_prefix, d.wb_start[FDOG_WBUCKETS] - d.wb_start[FDOG_WBUCKETS - 1]);
+    b.wide_total = d.wb_start[FDOG_WBUCKETS] - d.wb_start[FDOG_WBUCKETS - 1];
     for (int c = 0; c < kNumClasses; ++c) b.has_local[c] = d.cls_has_local[c];
     two(&b.slot_prefix, static_cast<int32_t>(S));
     b.slots_total = static_cast<int32_t>(S);
@@ -252,7 +252,6 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.cost, inst->cost.data(), sizeof(double) * n);
     up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
     up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
-    up(a.vrec, d.vrec.data(), sizeof(int32_t) * d.vrec.size());
     up(a.patterns, d.patterns.data(), sizeof(int32_t) * d.patterns.size());
     up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
     up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());

@@ -356,20 +356,6 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
     for (int64_t p = 0; p < slot; ++p)
         if (out.var[p] >= 0) out.csr_pos[fill[out.var[p]]++] = static_cast<int32_t>(p);
-    // per-variable 8-byte records: variables with one or two copies (most of
-    // them) carry their slots inline, so their multipliers are one dependent
-    // load away; longer lists are referenced into csr_pos
-    out.vrec.resize(2 * static_cast<size_t>(n_vars));
-    for (int32_t i = 0; i < n_vars; ++i) {
-        const int32_t b = out.csr_off[i], c = out.csr_off[i + 1] - b;
-        if (c == 1 || c == 2) {
-            out.vrec[2 * i] = out.csr_pos[b];
-            out.vrec[2 * i + 1] = c == 2 ? out.csr_pos[b + 1] : -1;
-        } else {
-            out.vrec[2 * i] = -(b + 1);
-            out.vrec[2 * i + 1] = c;
-        }
-    }
     // Tile-local variables: every copy in one tile (at most four copies) of a
     // row of at most kEpiMaxK layers.  The
     // update sweep computes their deferred term itself; the deferred-sum

@@ -50,7 +50,7 @@ int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& membe
     }
     // host image: InstDev[n], then the int32 prefix arrays
     const size_t desc_bytes = align_up(sizeof(InstDev) * n, 256);
-    const size_t n_ints = static_cast<size_t>(kNumClasses) * (2 * n + 1) + 6 * static_cast<size_t>(n + 1);
+    const size_t n_ints = static_cast<size_t>(kNumClasses) * (2 * n + 1) + 7 * static_cast<size_t>(n + 1);
     const size_t bytes = desc_bytes + sizeof(int32_t) * n_ints;
     if (v.cap < bytes) {
         if (v.dev) cudaFree(v.dev);
@@ -111,7 +111,10 @@ int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& membe
            [](fdog_instance* m) { return m->n_vars > 0 ? m->hdesc.n_obj_chunks : 0; });
     prefix(&b.tile_all_prefix, &b.tiles_all_total,
            [](fdog_instance* m) { return static_cast<int32_t>(m->dec.tiles.size()); });
-    prefix(&b.work_prefix, &b.work_total, [](fdog_instance* m) { return static_cast<int32_t>(m->dec.work.size()); });
+    prefix(&b.work_prefix, &b.work_total, [](fdog_instance* m) { return m->dec.wb_start[FDOG_WBUCKETS - 1]; });
+    prefix(&b.wide_prefix, &b.wide_total, [](fdog_instance* m) {
+        return m->dec.wb_start[FDOG_WBUCKETS] - m->dec.wb_start[FDOG_WBUCKETS - 1];
+    });
     if (!ids.empty()) {
         // a server keeps one module for every shape it has seen, so that views
         // of changing member sets do not each need a compile

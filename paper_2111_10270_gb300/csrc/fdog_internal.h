@@ -100,7 +100,7 @@ struct InstCtl {
 
 // Everything a kernel needs to know about one instance (device pointers).
 // deferred-sum work buckets: copy counts 1 .. FDOG_WBUCKETS - 1, then one
-// bucket for variables with more copies (read through vrec / csr_pos)
+// bucket for variables with more copies (a warp each, through csr_pos)
 #define FDOG_WBUCKETS 9
 
 struct InstDev {
@@ -115,8 +115,6 @@ struct InstDev {
     float* C;                // [n] target sum_j lambda^j_i (= c_i, perturbed by rounding)
     const int32_t* csr_off;  // [n + 1]
     const int32_t* csr_pos;  // [slots] padded slot positions of each variable, ascending
-    const int32_t* vrec;     // [2 n] per variable {a, b}: a >= 0: copies at slots a and b (b = -1: one copy);
-                             //       a < 0: |J_i| = b copies listed at csr_pos[-a - 1 ...]
     const int32_t* patterns; // [2 per pattern] {first entry, entries}: variables whose copies all lie in one tile
     const uint16_t* local_ent;  // [4 per entry] copy offsets (32 t + lane) within the tile, ascending, 0xFFFF unused
     const int32_t* work;     // [n_work] variables the deferred-sum kernel handles (copies in several tiles),
@@ -190,7 +188,6 @@ struct Decomposition {
     std::vector<int32_t> cls_tile_begin;  // kNumClasses + 1 (tiles sorted by class)
     std::vector<int32_t> var;      // padded slots
     std::vector<int32_t> csr_off, csr_pos;
-    std::vector<int32_t> vrec;     // 2 ints per variable (see InstDev::vrec)
     std::vector<int32_t> patterns;  // 2 ints per pattern (see InstDev::patterns)
     std::vector<uint16_t> local_ent;
     std::vector<int32_t> work;      // variables left to the deferred-sum kernel, bucketed by copy count
@@ -199,7 +196,7 @@ struct Decomposition {
     int32_t wb_pos[FDOG_WBUCKETS] = {0};
     int64_t n_local_vars = 0;
     int64_t n_work_slots = 0;       // copies of the variables in `work`
-    int64_t n_work_overflow = 0;    // of those, list entries read from csr_pos (variables with > 2 copies)
+    int64_t n_work_overflow = 0;    // of those, copies of variables with more than 8 (a warp each)
     bool cls_has_local[kNumClasses] = {false};
     std::vector<ShapeDev> shape_dev;
     std::vector<uint16_t> tpl;

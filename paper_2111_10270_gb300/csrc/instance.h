@@ -15,7 +15,7 @@ struct Engine;
 struct BatchView;
 
 // prefix ints of a one-instance batch: per class 3 (prefix[2], first[1]) + 4 x 2
-constexpr int kPrefixInts = 3 * kNumClasses + 12;
+constexpr int kPrefixInts = 3 * kNumClasses + 14;
 
 struct DevArrays {
     InstDev* inst = nullptr;
@@ -34,7 +34,6 @@ struct DevArrays {
     double* cost = nullptr;
     int32_t* csr_off = nullptr;
     int32_t* csr_pos = nullptr;
-    int32_t* vrec = nullptr;
     int32_t* patterns = nullptr;
     uint16_t* local_ent = nullptr;
     int32_t* work = nullptr;

@@ -45,32 +45,46 @@ __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     if (FDOG_INACTIVE(I->ctl)) return;
-    const int w = g - __ldg(a.prefix + ii);
+    const int w = g - __ldg(a.prefix + ii);  // below wb_start[FDOG_WBUCKETS - 1]: at most 8 copies
     const int i = I->work[w];  // a variable with copies in several tiles
     int b = 0;
 #pragma unroll
-    for (int q = 1; q < FDOG_WBUCKETS; ++q) b += w >= I->wb_start[q];
+    for (int q = 1; q < FDOG_WBUCKETS - 1; ++q) b += w >= I->wb_start[q];
+    // bucket of b + 1 copies: positions column by column, all loads independent;
+    // copies summed in ascending slot order (as in csr_pos), a fixed order
+    const int cnt = b + 1;
+    const int nb = I->wb_start[b + 1] - I->wb_start[b];
+    const int32_t* __restrict__ pos = I->wpos + I->wb_pos[b] + (w - I->wb_start[b]);
     const float* __restrict__ lam = I->lam;
-    float s = 0.f;  // copies in ascending slot order, as in csr_pos: a fixed summation order
-    int cnt;
-    if (b < FDOG_WBUCKETS - 1) {
-        // bucket of b + 1 copies: positions column by column, all loads independent
-        cnt = b + 1;
-        const int nb = I->wb_start[b + 1] - I->wb_start[b];
-        const int32_t* __restrict__ pos = I->wpos + I->wb_pos[b] + (w - I->wb_start[b]);
-        float l[FDOG_WBUCKETS - 1];
+    float l[FDOG_WBUCKETS - 1];
 #pragma unroll
-        for (int q = 0; q < FDOG_WBUCKETS - 1; ++q) l[q] = q < cnt ? lam[pos[q * nb]] : 0.f;
+    for (int q = 0; q < FDOG_WBUCKETS - 1; ++q) l[q] = q < cnt ? lam[pos[q * nb]] : 0.f;
+    float s = 0.f;
 #pragma unroll
-        for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
-            if (q < cnt) s += l[q];
-    } else {
-        const int2 r = reinterpret_cast<const int2*>(I->vrec)[i];
-        cnt = r.y;
-        const int32_t* __restrict__ pos = I->csr_pos + (-r.x - 1);
-        for (int p = 0; p < cnt; ++p) s += lam[pos[p]];
-    }
+    for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
+        if (q < cnt) s += l[q];
     I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
+}
+
+// Variables with more than 8 copies (one assignment variable of a matching
+// problem can sit in hundreds of rows): one warp per variable, lane l summing
+// copies l, l + 32, ... in ascending order, then a fixed butterfly.
+__global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (g >= a.total) return;
+    const int ii = find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    if (FDOG_INACTIVE(I->ctl)) return;
+    const int i = I->work[I->wb_start[FDOG_WBUCKETS - 1] + (g - __ldg(a.prefix + ii))];
+    const int b = I->csr_off[i], cnt = I->csr_off[i + 1] - b;
+    const int32_t* __restrict__ pos = I->csr_pos + b;
+    const float* __restrict__ lam = I->lam;
+    float s = 0.f;
+    for (int q = lane; q < cnt; q += 32) s += lam[pos[q]];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
 }
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
@@ -499,13 +513,19 @@ static FlatArgs flat(const DevBatch& b, const int32_t* prefix, int total) {
 }
 
 cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
-    if (b.work_total == 0) return cudaSuccess;
+    if (b.work_total == 0 && b.wide_total == 0) return cudaSuccess;
     const bool timed = cfg.prof && cfg.prof->on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-    reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
+    if (b.work_total > 0) {
+        reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
+        cfg.count();
+    }
+    if (b.wide_total > 0) {
+        reduce_T_wide_kernel<<<(b.wide_total + 7) / 8, 256, 0, s>>>(flat(b, b.wide_prefix, b.wide_total));
+        cfg.count();
+    }
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
-    cfg.count();
     return cudaGetLastError();
 }
 

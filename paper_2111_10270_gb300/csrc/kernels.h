@@ -41,8 +41,10 @@ struct DevBatch {
     int32_t vars_total = 0;
     int32_t* tile_all_prefix = nullptr;      // [n_inst + 1] all tiles of every class
     int32_t tiles_all_total = 0;
-    int32_t* work_prefix = nullptr;          // [n_inst + 1] variables left to the deferred-sum kernel
+    int32_t* work_prefix = nullptr;          // [n_inst + 1] deferred-sum variables with at most 8 copies
     int32_t work_total = 0;
+    int32_t* wide_prefix = nullptr;          // [n_inst + 1] deferred-sum variables with more copies (warp each)
+    int32_t wide_total = 0;
     bool has_local[kNumClasses] = {};        // some tile of the class has tile-local variables
     int32_t* slot_prefix = nullptr;          // [n_inst + 1] padded slots
     int32_t slots_total = 0;

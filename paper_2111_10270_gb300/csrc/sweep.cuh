@@ -363,45 +363,64 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
         const float omega = I->omega;
         const size_t base = static_cast<size_t>(tile.slot_base) + lane;
         float* __restrict__ lam = I->lam;
+        const int32_t* __restrict__ varp = I->var;
+        const float* __restrict__ Tv = I->T;
         constexpr bool update = MODE == kFwdUpdate || MODE == kBwdUpdate;
         const bool need_t = update || (a.flags & kMMAddT);
+        const bool add_t = (MODE == kMinMarg || MODE == kEval) && (a.flags & kMMAddT);
         const bool local = update && a.epi > 0 && tile.pattern >= 0;
 
-        // multiplier of layer t as sweep_kernel stages it (plus T in min-marginal
-        // and evaluation modes when asked), and the deferred term
-        auto load = [&](int t, float& l, float& tb) {
-            l = 0.f;
-            tb = 0.f;
-            if (valid) {
-                l = lam[base + static_cast<size_t>(t) * kTile];
-                if (need_t) tb = I->T[I->var[base + static_cast<size_t>(t) * kTile]];
+        // raw loads of one segment (multipliers, and variable ids if asked); independent of each other
+        auto fetch = [&](int s, float (&L)[C], int (&V)[C], bool with_var) {
+            const int t0 = s * C;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                L[c] = 0.f;
+                V[c] = -1;
+                if (valid && t0 + c < k) {
+                    const size_t p = base + static_cast<size_t>(t0 + c) * kTile;
+                    L[c] = lam[p];
+                    if (with_var) V[c] = varp[p];
+                }
             }
-            if constexpr (MODE == kMinMarg || MODE == kEval) {
-                if (a.flags & kMMAddT) l += tb;
+        };
+        // deferred terms of a fetched segment; with add_t the multipliers include them
+        auto terms = [&](float (&L)[C], const int (&V)[C], float (&Tt)[C]) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                Tt[c] = V[c] >= 0 ? Tv[V[c]] : 0.f;
+                if (add_t) L[c] += Tt[c];
             }
         };
 
         float term = 0.f;
         if constexpr (MODE == kFwdUpdate || MODE == kMinMarg || MODE == kEval) {
-            // SP(v, TOP) over the whole row; keep the labels at segment starts
+            // SP(v, TOP) over the whole row, one segment at a time from the last;
+            // keep the labels at segment starts
             float nx[W];
 #pragma unroll
             for (int v = 0; v < W; ++v) nx[v] = finf();
-#pragma unroll 4
-            for (int t = k - 1; t >= 0; --t) {
-                uint32_t c[W];
-                load_codes<W>(tpl + t * W, c);
-                float lt, tb;
-                load(t, lt, tb);
-                float cur[W];
+            for (int s = nseg - 1; s >= 0; --s) {
+                const int t0 = s * C;
+                const int kk = (k - t0 < C) ? k - t0 : C;
+                float L[C], Tt[C];
+                int V[C];
+                fetch(s, L, V, add_t);
+                if (add_t) terms(L, V, Tt);
 #pragma unroll
-                for (int v = 0; v < W; ++v) cur[v] = fminf(pick<W>(nx, c[v] & 0xFFu), pick<W>(nx, c[v] >> 8) + lt);
+                for (int cc = C - 1; cc >= 0; --cc) {
+                    if (cc < kk) {
+                        uint32_t c[W];
+                        load_codes<W>(tpl + (t0 + cc) * W, c);
+                        float cur[W];
 #pragma unroll
-                for (int v = 0; v < W; ++v) nx[v] = cur[v];
-                if (t % C == 0) {
+                        for (int v = 0; v < W; ++v) cur[v] = fminf(pick<W>(nx, c[v] & 0xFFu), pick<W>(nx, c[v] >> 8) + L[cc]);
 #pragma unroll
-                    for (int v = 0; v < W; ++v) cp[((t / C) * W + v) * kTile] = cur[v];
+                        for (int v = 0; v < W; ++v) nx[v] = cur[v];
+                    }
                 }
+#pragma unroll
+                for (int v = 0; v < W; ++v) cp[(s * W + v) * kTile] = nx[v];
             }
             if constexpr (MODE == kEval) term = nx[0];
         }
@@ -413,18 +432,22 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
             float negsum = 0.f, E = finf();
             float* __restrict__ mm0 = I->mm0;
             float* __restrict__ mm1 = I->mm1;
+            float Ln[C];
+            int Vn[C];
+            fetch(0, Ln, Vn, need_t);
             for (int s = 0; s < nseg; ++s) {
                 const int t0 = s * C;
                 const int kk = (k - t0 < C) ? k - t0 : C;
                 float L[C], Tt[C], Sg[C][W], nxt[W];
+                int V[C];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    L[c] = 0.f;
-                    Tt[c] = 0.f;
-                    if (c < kk) {
-                        load(t0 + c, L[c], Tt[c]);
-                        if (local && valid) ep_var[(t0 + c) * kTile + lane] = I->var[base + static_cast<size_t>(t0 + c) * kTile];
-                    }
+                for (int c = 0; c < C; ++c) { L[c] = Ln[c]; V[c] = Vn[c]; }
+                if (s + 1 < nseg) fetch(s + 1, Ln, Vn, need_t);  // in flight while this segment is swept
+                terms(L, V, Tt);
+                if (local && valid) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        if (c < kk) ep_var[(t0 + c) * kTile + lane] = V[c];
                 }
                 // labels of the segment's layers 1 .. kk-1, from the next checkpoint
 #pragma unroll
@@ -506,49 +529,58 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
         }
 
         if constexpr (MODE == kBwdUpdate) {
-            // SP(r, v) over the whole row; keep the labels at segment starts
+            // SP(r, v) over the whole row, one segment at a time; keep the labels at segment starts
             {
                 float f[W];
 #pragma unroll
                 for (int v = 0; v < W; ++v) f[v] = v == 0 ? 0.f : finf();
-#pragma unroll 4
-                for (int t = 0; t < k; ++t) {
-                    uint32_t c[W];
-                    load_codes<W>(tpl + t * W, c);
-                    float lt, tb;
-                    load(t, lt, tb);
-                    if (t % C == 0) {
+                for (int s = 0; s < nseg; ++s) {
+                    const int t0 = s * C;
+                    const int kk = (k - t0 < C) ? k - t0 : C;
+                    float L[C];
+                    int V[C];
+                    fetch(s, L, V, false);
 #pragma unroll
-                        for (int v = 0; v < W; ++v) cp[((t / C) * W + v) * kTile] = f[v];
+                    for (int v = 0; v < W; ++v) cp[(s * W + v) * kTile] = f[v];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        if (c < kk) {
+                            uint32_t cd[W];
+                            load_codes<W>(tpl + (t0 + c) * W, cd);
+                            float nf[W];
+#pragma unroll
+                            for (int v = 0; v < W; ++v) nf[v] = finf();
+#pragma unroll
+                            for (int v = 0; v < W; ++v) {
+                                push<W>(nf, cd[v] & 0xFFu, f[v]);
+                                push<W>(nf, cd[v] >> 8, f[v] + L[c]);
+                            }
+#pragma unroll
+                            for (int v = 0; v < W; ++v) f[v] = nf[v];
+                        }
                     }
-                    float nf[W];
-#pragma unroll
-                    for (int v = 0; v < W; ++v) nf[v] = finf();
-#pragma unroll
-                    for (int v = 0; v < W; ++v) {
-                        push<W>(nf, c[v] & 0xFFu, f[v]);
-                        push<W>(nf, c[v] >> 8, f[v] + lt);
-                    }
-#pragma unroll
-                    for (int v = 0; v < W; ++v) f[v] = nf[v];
                 }
             }
             float b[W];
 #pragma unroll
             for (int v = 0; v < W; ++v) b[v] = finf();
             float negsum = 0.f;
+            float Ln[C];
+            int Vn[C];
+            fetch(nseg - 1, Ln, Vn, true);
             for (int s = nseg - 1; s >= 0; --s) {
                 const int t0 = s * C;
                 const int kk = (k - t0 < C) ? k - t0 : C;
                 float L[C], Tt[C], Sg[C][W];
+                int V[C];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    L[c] = 0.f;
-                    Tt[c] = 0.f;
-                    if (c < kk) {
-                        load(t0 + c, L[c], Tt[c]);
-                        if (local && valid) ep_var[(t0 + c) * kTile + lane] = I->var[base + static_cast<size_t>(t0 + c) * kTile];
-                    }
+                for (int c = 0; c < C; ++c) { L[c] = Ln[c]; V[c] = Vn[c]; }
+                if (s > 0) fetch(s - 1, Ln, Vn, true);  // in flight while this segment is swept
+                terms(L, V, Tt);
+                if (local && valid) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        if (c < kk) ep_var[(t0 + c) * kTile + lane] = V[c];
                 }
                 // labels of the segment's layers, from its checkpoint
                 {

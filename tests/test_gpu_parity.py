@@ -194,6 +194,27 @@ def test_wide_and_long_rows_parity(P, oracle_mod, jit):
     assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
 
 
+@pytest.mark.parametrize("jit", [1, 0], ids=["specialised", "auto"])
+@pytest.mark.parametrize("kind", ["qap", "cell"])
+def test_qap_and_cell_tracking_parity(P, oracle_mod, kind, jit):
+    """The matching and tracking shapes at sizes the oracle runs in seconds:
+    assignment variables with dozens of copies (the warp-per-variable
+    deferred sums), AND rows, long in-flow rows (segmented sweeps), conflict
+    sets; bound trajectory and min-marginals against the oracle."""
+    ilp = ilpgen.qap(11, 14, 28, 6, 3) if kind == "qap" else ilpgen.cell_tracking(12, 5, 20, 60)
+    inst, orc, gl, ol, cond = trajectory(P, oracle_mod, ilp, 40, jit=jit)
+    kp = inst.kernel_plan()
+    if kind == "qap":
+        counts = np.bincount(orc.slot_vars(), minlength=ilp.n_vars)
+        assert counts.max() > 8, counts.max()
+    bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
+    assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL, kp
+
+
 def long_narrow_rows(seed=6):
     """Rows of width <= 4 and 9 .. 1000 layers: one-segment, multi-segment and
     ragged-segment shapes of the segmented kernels, some shapes filling more

@@ -273,6 +273,7 @@ int own_engine(fdog_instance* inst, Engine** eng, BatchView** view) {
     e.stream = inst->stream;
     e.cfg = inst->cfg;
     e.prof = &inst->prof;
+    engine_use_side(e);
     int rc = view_build(e, *inst->self_view, {inst});
     if (rc != FDOG_OK) {
         inst->last_error = e.err;
@@ -382,6 +383,65 @@ int ensure_mm1(fdog_instance* inst) {
     return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "descriptor update");
 }
 
+// Upload, initial dual state and (optionally) launch-shape tuning of a planned instance.
+int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool autotune) {
+    if (!inst) return FDOG_EINVAL;
+    if (inst->built) return FDOG_ESTATE;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        inst->last_error = "no CUDA device " + std::to_string(device);
+        return e != cudaSuccess ? FDOG_ECUDA : FDOG_EINVAL;
+    }
+    DeviceGuard g(device);
+    inst->device = device;
+    inst->stream = static_cast<cudaStream_t>(cuda_stream);
+    int rc = plan(inst);
+    if (rc != FDOG_OK) return rc;
+    const std::vector<int> ids = jit_ids(inst);
+    if (!ids.empty()) {
+        std::string why;
+        if (jit_kernels(ids, inst->jit, why) != FDOG_OK) {
+            // shape-specialised kernels unavailable: plan again for the generic kernels
+            inst->jit_note = why;
+            inst->jit_failed = true;
+            inst->planned = false;
+            if ((rc = plan(inst)) != FDOG_OK) return rc;
+        }
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "device properties");
+    inst->cfg.num_sms = prop.multiProcessorCount;
+    inst->cfg.warps_per_block = inst->params.block_threads > 0 ? inst->params.block_threads / 32 : 4;
+    inst->cfg.prof = &inst->prof;
+    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_ctl), sizeof(InstCtl));
+    if (e != cudaSuccess) { cudaGetLastError(); inst->host_ctl = nullptr; return FDOG_ENOMEM; }
+    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_x), std::max<size_t>(inst->n_vars, 1));
+    if (e != cudaSuccess) { cudaGetLastError(); inst->host_x = nullptr; return FDOG_ENOMEM; }
+    rc = allocate_and_upload(inst);
+    if (rc != FDOG_OK) return rc;
+    rc = reset_dual_state(inst);
+    if (rc != FDOG_OK) return rc;
+    e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "build");
+    inst->built = true;
+    if (autotune && inst->dec.n_bdds > 0) {
+        // launch shape of this instance's sweeps (results do not depend on it)
+        Engine* eng;
+        BatchView* v;
+        if ((rc = own_engine(inst, &eng, &v)) != FDOG_OK) return rc;
+        if ((rc = view_autotune(*eng, *v)) != FDOG_OK) {
+            inst->last_error = eng->err;
+            return rc;
+        }
+        inst->cfg.warps_per_block = eng->cfg.warps_per_block;
+        inst->cfg.max_waves = eng->cfg.max_waves;
+    }
+    return FDOG_OK;
+}
+
 }  // namespace fdog
 
 // ===========================================================================
@@ -477,48 +537,7 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
 
 int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream) {
     if (!inst) return FDOG_EINVAL;
-    if (inst->built) return FDOG_ESTATE;
-    int ndev = 0;
-    cudaError_t e = cudaGetDeviceCount(&ndev);
-    if (e != cudaSuccess || device < 0 || device >= ndev) {
-        cudaGetLastError();
-        inst->last_error = "no CUDA device " + std::to_string(device);
-        return e != cudaSuccess ? FDOG_ECUDA : FDOG_EINVAL;
-    }
-    DeviceGuard g(device);
-    inst->device = device;
-    inst->stream = static_cast<cudaStream_t>(cuda_stream);
-    int rc = plan(inst);
-    if (rc != FDOG_OK) return rc;
-    const std::vector<int> ids = jit_ids(inst);
-    if (!ids.empty()) {
-        std::string why;
-        if (jit_kernels(ids, inst->jit, why) != FDOG_OK) {
-            // shape-specialised kernels unavailable: plan again for the generic kernels
-            inst->jit_note = why;
-            inst->jit_failed = true;
-            inst->planned = false;
-            if ((rc = plan(inst)) != FDOG_OK) return rc;
-        }
-    }
-    cudaDeviceProp prop;
-    e = cudaGetDeviceProperties(&prop, device);
-    if (e != cudaSuccess) return fail_cuda(inst, e, "device properties");
-    inst->cfg.num_sms = prop.multiProcessorCount;
-    inst->cfg.warps_per_block = inst->params.block_threads > 0 ? inst->params.block_threads / 32 : 4;
-    inst->cfg.prof = &inst->prof;
-    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_ctl), sizeof(InstCtl));
-    if (e != cudaSuccess) { cudaGetLastError(); inst->host_ctl = nullptr; return FDOG_ENOMEM; }
-    e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_x), std::max<size_t>(inst->n_vars, 1));
-    if (e != cudaSuccess) { cudaGetLastError(); inst->host_x = nullptr; return FDOG_ENOMEM; }
-    rc = allocate_and_upload(inst);
-    if (rc != FDOG_OK) return rc;
-    rc = reset_dual_state(inst);
-    if (rc != FDOG_OK) return rc;
-    e = cudaStreamSynchronize(inst->stream);
-    if (e != cudaSuccess) return fail_cuda(inst, e, "build");
-    inst->built = true;
-    return FDOG_OK;
+    return build_instance(inst, device, cuda_stream, inst->params.block_threads == 0);
 }
 
 int fdog_plan(fdog_instance* inst, int64_t* device_bytes) {

@@ -45,6 +45,7 @@ int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream,
     e.cfg = insts[0]->cfg;
     e.cfg.prof = &b->prof;
     e.prof = nullptr;
+    engine_use_side(e);
     int rc = FDOG_OK;
     // members may have been built on other streams: their uploads must be complete
     for (fdog_instance* m : b->members)

@@ -280,6 +280,7 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
             out.fixed[i] = 2;
             out.const_lb += std::min(cost[i], 0.0);
         }
+        if (out.fixed[i] != -1) out.outside.push_back(i);
     }
     out.const_obj = out.const_lb;
 

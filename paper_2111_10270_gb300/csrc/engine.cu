@@ -31,6 +31,12 @@ BatchView::~BatchView() {
 Engine::~Engine() {
     if (dev_status) cudaFree(dev_status);
     if (host_status) cudaFreeHost(host_status);
+    side.destroy();
+}
+
+void engine_use_side(Engine& e) {
+    if (!e.side.ready && e.side.create(e.device) != cudaSuccess) cudaGetLastError();
+    e.cfg.side = e.side.ready ? &e.side : nullptr;
 }
 
 int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& members) {
@@ -185,7 +191,8 @@ int view_iterate(Engine& e, BatchView& v, int k) {
     int direct = k;
     cudaError_t ce = cudaSuccess;
     if (graphs && k >= e.chunk) {
-        if (!v.graph || v.graph_chunk != e.chunk || v.graph_wpb != e.cfg.warps_per_block) {
+        if (!v.graph || v.graph_chunk != e.chunk || v.graph_wpb != e.cfg.warps_per_block ||
+            v.graph_waves != e.cfg.max_waves || v.graph_side != (e.cfg.side != nullptr)) {
             v.drop_graph();
             LaunchCfg cap = e.cfg;
             Profiler counter;  // counts the captured launches once
@@ -205,6 +212,8 @@ int view_iterate(Engine& e, BatchView& v, int k) {
             }
             v.graph_chunk = e.chunk;
             v.graph_wpb = e.cfg.warps_per_block;
+            v.graph_waves = e.cfg.max_waves;
+            v.graph_side = e.cfg.side != nullptr;
             v.graph_launches_per_replay = counter.launches;
         }
         const int reps = k / e.chunk;
@@ -279,14 +288,13 @@ int finish_all(Engine& e, BatchView& v, const std::vector<int>& noconv) {
     if (rc != FDOG_OK) return rc;
     for (size_t i = 0; i < v.members.size(); ++i) {
         fdog_instance* m = v.members[i];
-        std::vector<uint8_t> x(m->n_vars, 0);
-        if (m->dec.n_bdds > 0) std::memcpy(x.data(), m->host_x, m->n_vars);
-        for (int32_t j = 0; j < m->n_vars; ++j) {
+        // variables in BDDs from the device; presolved and row-free ones from the plan
+        if (m->dec.n_bdds > 0) m->solution.assign(m->host_x, m->host_x + m->n_vars);
+        else m->solution.assign(static_cast<size_t>(m->n_vars), 0);
+        for (const int32_t j : m->dec.outside) {
             const int8_t f = m->dec.fixed[j];
-            if (f == 0 || f == 1) x[j] = static_cast<uint8_t>(f);
-            else if (f == 2) x[j] = m->cost[j] < 0 ? 1 : 0;
+            m->solution[j] = f == 2 ? (m->cost[j] < 0 ? 1 : 0) : static_cast<uint8_t>(f);
         }
-        m->solution = std::move(x);
         m->objective = (m->dec.n_bdds > 0 ? st[i].objective : 0.0) + m->dec.const_obj;
         m->feasible = st[i].n_rejected == 0 ? 1 : 0;
         m->has_solution = true;
@@ -438,13 +446,15 @@ int view_autotune(Engine& e, BatchView& v) {
     if (v.b.n_inst == 0) return FDOG_OK;
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return fail(e, cudaGetLastError(), "autotune");
-    const int saved = e.cfg.warps_per_block;
-    int best = saved;
+    int best = e.cfg.warps_per_block, best_waves = e.cfg.max_waves;
     float best_ms = 1e30f;
     LaunchCfg cfg = e.cfg;
     cfg.prof = nullptr;
-    for (int wpb : {2, 4, 8}) {
+    // warps per block x grid mode (one persistent wave, or a block per tile group)
+    for (int combo = 0; combo < 6; ++combo) {
+        const int wpb = 2 << (combo % 3), waves = combo < 3 ? 1 : 0;
         cfg.warps_per_block = wpb;
+        cfg.max_waves = waves;
         cudaError_t ce = launch_sweep(v.b, kMinMarg, 0, cfg, e.stream);  // warm-up
         if (ce == cudaSuccess) ce = cudaEventRecord(a, e.stream);
         for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch_sweep(v.b, kMinMarg, 0, cfg, e.stream);
@@ -457,11 +467,12 @@ int view_autotune(Engine& e, BatchView& v) {
             cudaEventDestroy(z);
             return fail(e, ce, "autotune");
         }
-        if (ms < best_ms) { best_ms = ms; best = wpb; }
+        if (ms < best_ms) { best_ms = ms; best = wpb; best_waves = waves; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(z);
     e.cfg.warps_per_block = best;
+    e.cfg.max_waves = best_waves;
     return FDOG_OK;
 }
 

@@ -26,6 +26,8 @@ struct BatchView {
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     int graph_wpb = 0;
+    int graph_waves = -1;
+    bool graph_side = false;
     int64_t graph_launches_per_replay = 0;
     BatchView() = default;
     BatchView(const BatchView&) = delete;
@@ -46,9 +48,14 @@ struct Engine {
     InstStatus* dev_status = nullptr;
     InstStatus* host_status = nullptr;  // pinned
     int status_cap = 0;
+    SideStreams side;  // created by engine_use_side; cfg.side points here once they exist
     std::string err;
     ~Engine();
 };
+
+// Creates the engine's side streams on its device (once) and points cfg at
+// them; without them every launch stays in order on the engine's stream.
+void engine_use_side(Engine& e);
 
 // Lays out `members` (built on the engine's device) as one batch.
 int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& members);
@@ -81,8 +88,9 @@ int engine_admit(Engine& e, std::vector<Member>& ms, size_t first, int max_iters
 // reaching kPhaseDone are finished (objective, acceptance, solution copied).
 int engine_step(Engine& e, std::vector<Member>& ms);
 
-// Picks the sweep kernels' warps per block for this view by timing
-// min-marginal sweeps (they write only scratch, so the dual state is untouched).
+// Picks the sweep kernels' warps per block and grid mode for this view by
+// timing min-marginal sweeps (they write only scratch, so the dual state is
+// untouched; results do not depend on either choice).
 int view_autotune(Engine& e, BatchView& v);
 
 // Alg. 2 for every member (which must have finished their dual phase):

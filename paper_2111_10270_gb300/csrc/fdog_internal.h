@@ -175,6 +175,7 @@ struct HostShape {
 struct Decomposition {
     // presolve
     std::vector<int8_t> fixed;     // -1 in a BDD, 0/1 fixed, 2 in no row
+    std::vector<int32_t> outside;  // variables with fixed != -1 (their value is set on the host)
     double const_lb = 0.0;         // sum fixed c x + sum free min(c, 0)
     double const_obj = 0.0;        // sum fixed c x + sum free c [c < 0]
     // BDDs in layout order

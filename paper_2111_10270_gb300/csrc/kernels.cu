@@ -466,46 +466,118 @@ int smem_max_layers(int width) {
     return (200 * 1024 - kEpiMaxK * 2 * kTile * 4) / (kTile * 4 * (2 + width));
 }
 
-cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
-    for (int cls = 0; cls < kNumClasses; ++cls) {
-        const int total = b.tiles_total[cls];
-        if (total == 0) continue;
-        const bool reg = class_is_reg(cls);
-        const int W = class_width(cls);
-        int wpb = cfg.warps_per_block;
-        const bool seg = class_is_seg(cls);
-        // staged kernels: one row of state per layer; segmented kernels: one checkpoint per kRegK layers
-        const int kstride = reg ? 0 : (seg ? (b.kmax[cls] + kRegK - 1) / kRegK : b.kmax[cls]);
-        const int epi = ((mode == kFwdUpdate || mode == kBwdUpdate) && b.has_local[cls])
-                            ? (b.kmax[cls] < kEpiMaxK ? b.kmax[cls] : kEpiMaxK) : 0;
-        const size_t per_warp =
-            (static_cast<size_t>(kstride) * (seg ? W : 2 + W) + static_cast<size_t>(epi) * 2) * kTile * sizeof(float);
-        while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
-        const size_t smem = per_warp * wpb;
-        SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags, epi};
-        const int blocks = blocks_for(total, wpb, cfg.num_sms * (2048 / (32 * wpb)));
-        const bool timed = cfg.prof && cfg.prof->on && (mode == kFwdUpdate || mode == kBwdUpdate);
-        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-        if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-        cudaError_t e;
-        if (cls == kJitClass) {
-            void* kargs[] = {&args};
-            e = cudaSuccess;
-            if (smem > 48 * 1024)
-                e = cudaFuncSetAttribute(b.jit.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-            if (e == cudaSuccess) e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, smem, s);
-        } else switch (W) {
-            case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-            case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-            case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-            default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-        }
-        if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(true, ev0, ev1); }
-        cfg.count();
-        if (e != cudaSuccess) return e;
+namespace {
+
+// one class's sweep launch on stream s
+cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
+    const int total = b.tiles_total[cls];
+    const bool reg = class_is_reg(cls);
+    const int W = class_width(cls);
+    int wpb = cfg.warps_per_block;
+    const bool seg = class_is_seg(cls);
+    // staged kernels: one row of state per layer; segmented kernels: one checkpoint per kRegK layers
+    const int kstride = reg ? 0 : (seg ? (b.kmax[cls] + kRegK - 1) / kRegK : b.kmax[cls]);
+    const int epi = ((mode == kFwdUpdate || mode == kBwdUpdate) && b.has_local[cls])
+                        ? (b.kmax[cls] < kEpiMaxK ? b.kmax[cls] : kEpiMaxK) : 0;
+    const size_t per_warp =
+        (static_cast<size_t>(kstride) * (seg ? W : 2 + W) + static_cast<size_t>(epi) * 2) * kTile * sizeof(float);
+    while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb >>= 1;
+    const size_t smem = per_warp * wpb;
+    SweepArgs args{b.insts, b.tile_prefix[cls], b.tile_first[cls], b.n_inst, total, kstride, mm_flags, epi};
+    const int blocks = blocks_for(total, wpb, cfg.max_waves > 0 ? cfg.max_waves * cfg.num_sms * (2048 / (32 * wpb)) : (1 << 30));
+    const bool timed = cfg.prof && cfg.prof->on && (mode == kFwdUpdate || mode == kBwdUpdate);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+    cudaError_t e;
+    if (cls == kJitClass) {
+        void* kargs[] = {&args};
+        e = cudaSuccess;
+        if (smem > 48 * 1024)
+            e = cudaFuncSetAttribute(b.jit.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem));
+        if (e == cudaSuccess) e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, smem, s);
+    } else switch (W) {
+        case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+        case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+        case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+        default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
     }
+    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(true, ev0, ev1); }
+    cfg.count();
+    return e;
+}
+
+bool can_fork(const LaunchCfg& cfg) { return cfg.side && cfg.side->ready && !(cfg.prof && cfg.prof->on); }
+
+}  // namespace
+
+int SideStreams::create(int device) {
+    if (ready) return cudaSuccess;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    int lo = 0, hi = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (int j = 0; j < kSideStreams && e == cudaSuccess; ++j)
+        e = cudaStreamCreateWithPriority(&s[j], cudaStreamNonBlocking, hi);  // small latency-bound work first
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int j = 0; j < kSideStreams && e == cudaSuccess; ++j) e = cudaEventCreateWithFlags(&join[j], cudaEventDisableTiming);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        destroy();
+        return e;
+    }
+    ready = true;
     return cudaSuccess;
+}
+
+void SideStreams::destroy() {
+    for (int j = 0; j < kSideStreams; ++j) {
+        if (s[j]) cudaStreamDestroy(s[j]);
+        if (join[j]) cudaEventDestroy(join[j]);
+        s[j] = nullptr;
+        join[j] = nullptr;
+    }
+    if (fork) cudaEventDestroy(fork);
+    fork = nullptr;
+    ready = false;
+}
+
+// All classes of one pass.  With side streams, the minor classes are
+// launched first on them (their blocks become resident before the dominant
+// launch fills the GPU) and joined back before the pass ends.
+cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
+    int cls_list[kNumClasses], n = 0, dom = -1;
+    long long best = -1;
+    for (int cls = 0; cls < kNumClasses; ++cls) {
+        if (b.tiles_total[cls] == 0) continue;
+        cls_list[n++] = cls;
+        const long long work = static_cast<long long>(b.tiles_total[cls]) * (b.kmax[cls] > 0 ? b.kmax[cls] : 1);
+        if (work > best) { best = work; dom = cls; }
+    }
+    cudaError_t e = cudaSuccess;
+    if (n <= 1 || !can_fork(cfg)) {
+        for (int q = 0; q < n && e == cudaSuccess; ++q) e = launch_class(b, cls_list[q], mode, mm_flags, cfg, s);
+        return e;
+    }
+    const SideStreams& sd = *cfg.side;
+    bool used[kSideStreams] = {};
+    e = cudaEventRecord(sd.fork, s);
+    int j = 0;
+    for (int q = 0; q < n && e == cudaSuccess; ++q) {
+        if (cls_list[q] == dom) continue;
+        const int k = j++ % kSideStreams;
+        if (!used[k]) { e = cudaStreamWaitEvent(sd.s[k], sd.fork, 0); used[k] = true; }
+        if (e == cudaSuccess) e = launch_class(b, cls_list[q], mode, mm_flags, cfg, sd.s[k]);
+    }
+    if (e == cudaSuccess) e = launch_class(b, dom, mode, mm_flags, cfg, s);
+    for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
+        if (!used[k]) continue;
+        e = cudaEventRecord(sd.join[k], sd.s[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, sd.join[k], 0);
+    }
+    return e;
 }
 
 static FlatArgs flat(const DevBatch& b, const int32_t* prefix, int total) {
@@ -517,13 +589,25 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
     const bool timed = cfg.prof && cfg.prof->on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+    // the warp-per-variable kernel on a side stream when both have work (disjoint variables)
+    const bool fork = b.work_total > 0 && b.wide_total > 0 && can_fork(cfg);
+    cudaStream_t ws = s;
+    if (fork) {
+        cudaEventRecord(cfg.side->fork, s);
+        cudaStreamWaitEvent(cfg.side->s[0], cfg.side->fork, 0);
+        ws = cfg.side->s[0];
+    }
+    if (b.wide_total > 0) {
+        reduce_T_wide_kernel<<<(b.wide_total + 7) / 8, 256, 0, ws>>>(flat(b, b.wide_prefix, b.wide_total));
+        cfg.count();
+    }
     if (b.work_total > 0) {
         reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
         cfg.count();
     }
-    if (b.wide_total > 0) {
-        reduce_T_wide_kernel<<<(b.wide_total + 7) / 8, 256, 0, s>>>(flat(b, b.wide_prefix, b.wide_total));
-        cfg.count();
+    if (fork) {
+        cudaEventRecord(cfg.side->join[0], ws);
+        cudaStreamWaitEvent(s, cfg.side->join[0], 0);
     }
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
     return cudaGetLastError();

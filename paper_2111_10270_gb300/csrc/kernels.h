@@ -70,10 +70,27 @@ struct Profiler {
     void release();
 };
 
+// Streams beside the launching stream for the small launches of a pass
+// (minor kernel classes, the warp-per-variable deferred sums): forked from
+// and joined back into the launching stream around each pass, so that they
+// run alongside the dominant launch, in eager mode and inside graphs alike.
+constexpr int kSideStreams = 3;
+struct SideStreams {
+    cudaStream_t s[kSideStreams] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kSideStreams] = {};
+    bool ready = false;
+    int create(int device);  // cudaError_t as int
+    void destroy();
+};
+
 struct LaunchCfg {
     int warps_per_block = 4;  // sweep kernels
     int num_sms = 152;
+    int max_waves = 1;        // sweep grid: at most this many waves of resident blocks (0: a block per
+                              // warps_per_block tiles), the rest by a grid-stride loop
     Profiler* prof = nullptr;
+    const SideStreams* side = nullptr;  // no side streams: every launch in order on the stream
     void count(int n = 1) const {
         if (prof) prof->launches += n;
     }

@@ -78,6 +78,7 @@ int plan(fdog_instance* inst, bool compile_jit);
 size_t arena_size(const fdog_instance* inst);
 std::vector<int> jit_ids(const fdog_instance* inst);
 int release_device(fdog_instance* inst);
+int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool autotune);
 }  // namespace fdog
 
 namespace {
@@ -111,7 +112,7 @@ void worker_main(fdog_server* s) {
         const double t0 = now_s();
         const size_t first = s->active.size();
         for (Job* j : admit) {
-            int rc = fdog_build_bdds(j->inst, s->device, s->stream);
+            int rc = build_instance(j->inst, s->device, s->stream, false);  // the server's engine sets launch shapes
             std::lock_guard<std::mutex> lk(s->mu);
             if (rc != FDOG_OK) {
                 s->used -= j->bytes;
@@ -210,6 +211,7 @@ int fdog_server_create(int32_t device, int64_t hbm_budget, int32_t max_active, i
     e.cfg.warps_per_block = 4;
     e.cfg.prof = &s->prof;
     e.prof = nullptr;
+    engine_use_side(e);
     s->worker = std::thread(worker_main, s);
     *out = s;
     return FDOG_OK;

@@ -74,6 +74,11 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *   seed = 0                   seed of the counter-based perturbation draws
  *   block_threads = 0          threads per CTA for the sweep kernels;
  *                              0 = use the built-in autotuner
+ *   grid_waves = 0             sweep grid size: k > 0 = at most k waves of
+ *                              resident CTAs (grid-stride loop beyond),
+ *                              -1 = one CTA per group of tiles; 0 = chosen by
+ *                              the autotuner (block_threads = 0) or one wave.
+ *                              Results do not depend on either setting.
  *   jit = 0                    shape-specialised sweep kernels, compiled with
  *                              NVRTC for BDD shapes of width <= 4 and length
  *                              <= 16: 0 = for such shapes with at least 4096
@@ -98,7 +103,8 @@ typedef struct {
     int32_t block_threads;
     int32_t jit;
     int32_t fuse;
-    int32_t reserved[5];
+    int32_t grid_waves;
+    int32_t reserved[4];
 } fdog_params;
 
 /* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */

@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("jit", ctypes.c_int32),
         ("fuse", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("grid_waves", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

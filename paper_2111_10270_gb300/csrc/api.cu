@@ -415,6 +415,7 @@ int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool 
     if (e != cudaSuccess) return fail_cuda(inst, e, "device properties");
     inst->cfg.num_sms = prop.multiProcessorCount;
     inst->cfg.warps_per_block = inst->params.block_threads > 0 ? inst->params.block_threads / 32 : 4;
+    inst->cfg.max_waves = inst->params.grid_waves > 0 ? inst->params.grid_waves : (inst->params.grid_waves < 0 ? 0 : 1);
     inst->cfg.prof = &inst->prof;
     e = cudaMallocHost(reinterpret_cast<void**>(&inst->host_ctl), sizeof(InstCtl));
     if (e != cudaSuccess) { cudaGetLastError(); inst->host_ctl = nullptr; return FDOG_ENOMEM; }
@@ -432,7 +433,7 @@ int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool 
         Engine* eng;
         BatchView* v;
         if ((rc = own_engine(inst, &eng, &v)) != FDOG_OK) return rc;
-        if ((rc = view_autotune(*eng, *v)) != FDOG_OK) {
+        if ((rc = view_autotune(*eng, *v, inst->params.grid_waves == 0)) != FDOG_OK) {
             inst->last_error = eng->err;
             return rc;
         }
@@ -462,6 +463,7 @@ int fdog_params_default(fdog_params* p) {
     p->max_rounds = 200;
     p->seed = 0;
     p->block_threads = 0;
+    p->grid_waves = 0;
     return FDOG_OK;
 }
 
@@ -491,7 +493,7 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
     if (params) p = *params; else fdog_params_default(&p);
     if (!(p.omega > 0.0 && p.omega <= 1.0) || !(p.delta > 0.0) || !(p.alpha >= 1.0) || p.window < 1 ||
         p.window >= kLbRing || p.min_iters < 0 || p.rounding_dual_iters < 0 || p.max_rounds < 0 ||
-        p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0)
+        p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0 || p.grid_waves < -1)
         return FDOG_EINVAL;
     for (int32_t i = 0; i < n_vars; ++i)
         if (!std::isfinite(cost[i])) return FDOG_EINVAL;

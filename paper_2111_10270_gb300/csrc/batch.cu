@@ -53,7 +53,7 @@ int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream,
     if (rc == FDOG_OK && insts[0]->params.block_threads == 0) {
         BatchView v;
         rc = view_build(e, v, b->members);
-        if (rc == FDOG_OK) rc = view_autotune(e, v);
+        if (rc == FDOG_OK) rc = view_autotune(e, v, insts[0]->params.grid_waves == 0);
     }
     if (prev >= 0 && prev != dev) cudaSetDevice(prev);
     if (rc != FDOG_OK) {

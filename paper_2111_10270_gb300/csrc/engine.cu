@@ -442,7 +442,7 @@ int engine_solve(Engine& e, const std::vector<fdog_instance*>& members, int max_
     return FDOG_OK;
 }
 
-int view_autotune(Engine& e, BatchView& v) {
+int view_autotune(Engine& e, BatchView& v, bool tune_grid) {
     if (v.b.n_inst == 0) return FDOG_OK;
     cudaEvent_t a = nullptr, z = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) return fail(e, cudaGetLastError(), "autotune");
@@ -451,8 +451,8 @@ int view_autotune(Engine& e, BatchView& v) {
     LaunchCfg cfg = e.cfg;
     cfg.prof = nullptr;
     // warps per block x grid mode (one persistent wave, or a block per tile group)
-    for (int combo = 0; combo < 6; ++combo) {
-        const int wpb = 2 << (combo % 3), waves = combo < 3 ? 1 : 0;
+    for (int combo = 0; combo < (tune_grid ? 6 : 3); ++combo) {
+        const int wpb = 2 << (combo % 3), waves = tune_grid ? (combo < 3 ? 1 : 0) : e.cfg.max_waves;
         cfg.warps_per_block = wpb;
         cfg.max_waves = waves;
         cudaError_t ce = launch_sweep(v.b, kMinMarg, 0, cfg, e.stream);  // warm-up

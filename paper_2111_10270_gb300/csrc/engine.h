@@ -91,7 +91,7 @@ int engine_step(Engine& e, std::vector<Member>& ms);
 // Picks the sweep kernels' warps per block and grid mode for this view by
 // timing min-marginal sweeps (they write only scratch, so the dual state is
 // untouched; results do not depend on either choice).
-int view_autotune(Engine& e, BatchView& v);
+int view_autotune(Engine& e, BatchView& v, bool tune_grid = true);
 
 // Alg. 2 for every member (which must have finished their dual phase):
 // add-back, rounds of test / perturb / re-optimise, objective, acceptance,

@@ -391,15 +391,17 @@ def test_runs_are_bitwise_deterministic(P):
     assert outs[0] == outs[1]
 
 
-def test_block_size_does_not_change_results(P):
+def test_launch_shape_does_not_change_results(P):
+    """Warps per block, grid size (one persistent wave, two waves, a block
+    per tile group) and the autotuned choice: bitwise the same results."""
     g = ilpgen.mrf_grid(16, 16, 3, 4)
     res = []
-    for bt in (64, 128, 256):
-        inst = gpu_instance(P, g, block_threads=bt)
+    for bt, waves in ((64, 1), (128, 1), (256, 1), (128, 2), (128, -1), (64, -1), (0, 0)):
+        inst = gpu_instance(P, g, block_threads=bt, grid_waves=waves)
         inst.iterate(25)
         _, _, lam = inst.multipliers()
         res.append((inst.lower_bound(), lam.tobytes()))
-    assert res[0] == res[1] == res[2]
+    assert all(r == res[0] for r in res)
 
 
 def test_checkpoint_resume_is_bit_identical(P):

@@ -289,12 +289,14 @@ int fdog_transfer_bytes(fdog_instance* inst, int64_t* h2d, int64_t* d2h);
 
 /*
  * Kernel timing.  While profiling is on, every update-pass sweep launch (the
- * ascending / descending passes of Alg. 1) and every per-variable
- * deferred-sum launch is bracketed by CUDA events on the instance's stream.
- * fdog_profile_read synchronises the stream and returns the launches and
- * summed device milliseconds of both kernels recorded since the last read,
- * plus *kernel_launches = all kernel launches of the instance since it was
- * built (always counted).  Any output pointer may be NULL.
+ * ascending / descending passes of Alg. 1) and every deferred-sum step is
+ * bracketed by CUDA events on the stream it runs on (iteration graphs are
+ * not used meanwhile).  fdog_profile_read synchronises the stream and
+ * returns, since the last read, the launches and summed device milliseconds
+ * of the sweeps of each pass's dominant kernel class (the one with the most
+ * tile-layers) and of the deferred-sum steps, plus *kernel_launches = all
+ * kernel launches of the instance since it was built (always counted).  Any
+ * output pointer may be NULL.
  */
 int fdog_set_profiling(fdog_instance* inst, int32_t on);
 int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* sweep_ms, int64_t* reduce_launches,

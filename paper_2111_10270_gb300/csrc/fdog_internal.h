@@ -69,6 +69,7 @@ struct TileDev {
 };
 
 #define FDOG_LB_RING 64
+#define FDOG_LB_CHUNK 256      // tiles per chunk of the lower-bound reduction
 
 // Device-resident control block of one instance.
 struct InstCtl {
@@ -89,9 +90,10 @@ struct InstCtl {
     int32_t n_rejected;       // BDDs whose row the rounded solution violates
     int32_t iter_limit;       // update kernels skip the instance once iter reaches it
     int32_t round;            // rounding: current round of Alg. 2
-    int32_t pad1;
+    int32_t staged;           // this iteration's bound is reduced into lb_staged, not yet committed
     double tol;
     double delta;             // rounding: current perturbation strength
+    double lb_staged;
 };
 
 // True when the update kernels must leave the instance alone: its stopping

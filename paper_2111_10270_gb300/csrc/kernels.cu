@@ -167,6 +167,19 @@ __device__ __forceinline__ void block_pair_reduce(double* ss, double* sc, double
     }
 }
 
+// bound of a finished iteration: ring, counter, stopping test (Alg. 1 text)
+__device__ __forceinline__ void commit_iteration(InstCtl* ctl, double lb) {
+    const int it = ctl->iter;
+    ctl->lb_ring[it % kLbRing] = lb;
+    ctl->lb_last = lb;
+    ctl->iter = it + 1;
+    const int since = ++ctl->since_reset;
+    if (ctl->stop_enabled && since >= ctl->min_iters && since > ctl->window) {
+        const double prev = ctl->lb_ring[(it - ctl->window) % kLbRing];
+        if (lb - prev <= ctl->tol * fmax(fabs(lb), 1.0)) ctl->done = 1;
+    }
+}
+
 // One block per chunk of kLbChunk tiles (one tile per thread), then the last
 // block of the instance sums the chunk partials.  The chunking depends only
 // on the instance, so its bound is the same alone or in a batch.
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     InstCtl* ctl = I->ctl;
-    if (a.target == kLbIterate && FDOG_INACTIVE(ctl)) return;
+    if (a.target != kLbEval && FDOG_INACTIVE(ctl)) return;
     const int c = g - __ldg(a.prefix + ii);
     const int t = c * kLbChunk + threadIdx.x;
     // the chunk's tile partials as compensated FP32 pairs (FP64 is a small
@@ -202,19 +215,26 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
         const double lb = S + Cc;
         ctl->ticket = 0;
         if (a.target == kLbIterate) {
-            const int it = ctl->iter;
-            ctl->lb_ring[it % kLbRing] = lb;
-            ctl->lb_last = lb;
-            ctl->iter = it + 1;
-            const int since = ++ctl->since_reset;
-            if (ctl->stop_enabled && since >= ctl->min_iters && since > ctl->window) {
-                const double prev = ctl->lb_ring[(it - ctl->window) % kLbRing];
-                if (lb - prev <= ctl->tol * fmax(fabs(lb), 1.0)) ctl->done = 1;
-            }
+            commit_iteration(ctl, lb);
+        } else if (a.target == kLbStage) {
+            ctl->lb_staged = lb;
+            ctl->staged = 1;
         } else {
             ctl->lb_eval = lb;
         }
     }
+}
+
+// End of an iteration for every member whose bound was staged: ring, counter
+// and the stopping test.  Runs after the deferred sums of the backward pass,
+// which must still see the iteration as active.
+__global__ void lb_commit_kernel(const InstDev* insts, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    InstCtl* ctl = insts[i].ctl;
+    if (!ctl->staged) return;
+    ctl->staged = 0;
+    commit_iteration(ctl, ctl->lb_staged);
 }
 
 // C_i = c_i, T_i = 0 (M-bar = 0)
@@ -469,7 +489,8 @@ int smem_max_layers(int width) {
 namespace {
 
 // one class's sweep launch on stream s
-cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s) {
+cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s,
+                         bool dominant) {
     const int total = b.tiles_total[cls];
     const bool reg = class_is_reg(cls);
     const int W = class_width(cls);
@@ -502,12 +523,13 @@ cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, con
         case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
         default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
     }
-    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(true, ev0, ev1); }
+    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(dominant ? 0 : 2, ev0, ev1); }
     cfg.count();
     return e;
 }
 
-bool can_fork(const LaunchCfg& cfg) { return cfg.side && cfg.side->ready && !(cfg.prof && cfg.prof->on); }
+// timing, when on, records each launch's events on the stream it runs on
+bool can_fork(const LaunchCfg& cfg) { return cfg.side && cfg.side->ready; }
 
 }  // namespace
 
@@ -558,7 +580,8 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
     }
     cudaError_t e = cudaSuccess;
     if (n <= 1 || !can_fork(cfg)) {
-        for (int q = 0; q < n && e == cudaSuccess; ++q) e = launch_class(b, cls_list[q], mode, mm_flags, cfg, s);
+        for (int q = 0; q < n && e == cudaSuccess; ++q)
+            e = launch_class(b, cls_list[q], mode, mm_flags, cfg, s, cls_list[q] == dom);
         return e;
     }
     const SideStreams& sd = *cfg.side;
@@ -569,9 +592,9 @@ cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const Launch
         if (cls_list[q] == dom) continue;
         const int k = j++ % kSideStreams;
         if (!used[k]) { e = cudaStreamWaitEvent(sd.s[k], sd.fork, 0); used[k] = true; }
-        if (e == cudaSuccess) e = launch_class(b, cls_list[q], mode, mm_flags, cfg, sd.s[k]);
+        if (e == cudaSuccess) e = launch_class(b, cls_list[q], mode, mm_flags, cfg, sd.s[k], false);
     }
-    if (e == cudaSuccess) e = launch_class(b, dom, mode, mm_flags, cfg, s);
+    if (e == cudaSuccess) e = launch_class(b, dom, mode, mm_flags, cfg, s, true);
     for (int k = 0; k < kSideStreams && e == cudaSuccess; ++k) {
         if (!used[k]) continue;
         e = cudaEventRecord(sd.join[k], sd.s[k]);
@@ -609,7 +632,7 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
         cudaEventRecord(cfg.side->join[0], ws);
         cudaStreamWaitEvent(s, cfg.side->join[0], 0);
     }
-    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(false, ev0, ev1); }
+    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(1, ev0, ev1); }
     return cudaGetLastError();
 }
 
@@ -636,14 +659,19 @@ void Profiler::drain(int64_t& n_sweep, double& ms_sweep, int64_t& n_reduce, doub
     };
     sum(sweep, n_sweep, ms_sweep);
     sum(reduce, n_reduce, ms_reduce);
+    int64_t n_minor = 0;
+    double ms_minor = 0.0;
+    sum(minor, n_minor, ms_minor);
     cudaGetLastError();
 }
 
 void Profiler::release() {
     for (auto& [a, b] : sweep) { pool.push_back(a); pool.push_back(b); }
     for (auto& [a, b] : reduce) { pool.push_back(a); pool.push_back(b); }
+    for (auto& [a, b] : minor) { pool.push_back(a); pool.push_back(b); }
     sweep.clear();
     reduce.clear();
+    minor.clear();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     pool.clear();
 }
@@ -734,8 +762,23 @@ cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream
     if ((e = launch_sweep(b, kFwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_sweep(b, kBwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
+    // the bound reduction and the deferred sums both read only the pass's output
+    // (tile partials, multipliers) and write disjoint state: side by side
+    const bool fork = can_fork(cfg) && b.chunks_total > 0;
+    if (fork) {
+        if ((e = cudaEventRecord(cfg.side->fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(cfg.side->s[1], cfg.side->fork, 0)) != cudaSuccess) return e;
+    }
+    if ((e = launch_lb_reduce(b, kLbStage, cfg, fork ? cfg.side->s[1] : s)) != cudaSuccess) return e;
     if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
-    return launch_lb_reduce(b, kLbIterate, cfg, s);
+    if (fork) {
+        if ((e = cudaEventRecord(cfg.side->join[1], cfg.side->s[1])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, cfg.side->join[1], 0)) != cudaSuccess) return e;
+    }
+    if (b.n_inst == 0) return cudaSuccess;
+    cfg.count();
+    lb_commit_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst);
+    return cudaGetLastError();
 }
 
 }  // namespace fdog

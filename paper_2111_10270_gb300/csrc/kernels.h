@@ -24,8 +24,9 @@ constexpr int kMMBoth = 2;   // write m0 and m1 (else M = m1 - m0 into mm0)
 // lower-bound reduction targets
 constexpr int kLbIterate = 0;  // running bound of an iteration: ring, counter, stopping rule
 constexpr int kLbEval = 1;     // evaluation: InstCtl::lb_eval
+constexpr int kLbStage = 2;    // bound of an iteration into InstCtl::lb_staged (committed later)
 
-constexpr int kLbChunk = 256;    // tiles per block of the lower-bound reduction (one per thread)
+constexpr int kLbChunk = FDOG_LB_CHUNK;  // tiles per chunk of the lower-bound reduction
 constexpr int kObjChunk = 8192;  // variables per block of the objective reduction
 
 // Device-side description of a batch of instances (one or many).  Work of
@@ -62,9 +63,12 @@ struct Profiler {
     bool on = false;
     int64_t launches = 0;  // kernel launches of this instance (always counted)
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep, reduce;
+    // update sweeps of the dominant class of each pass, deferred-sum steps, other sweep launches
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep, reduce, minor;
     cudaEvent_t take();
-    void record(bool is_sweep, cudaEvent_t a, cudaEvent_t b) { (is_sweep ? sweep : reduce).emplace_back(a, b); }
+    void record(int kind, cudaEvent_t a, cudaEvent_t b) {
+        (kind == 0 ? sweep : kind == 1 ? reduce : minor).emplace_back(a, b);
+    }
     // sums and recycles the recorded pairs (the stream must be synchronised)
     void drain(int64_t& n_sweep, double& ms_sweep, int64_t& n_reduce, double& ms_reduce);
     void release();

@@ -138,7 +138,7 @@ void emit_shape(std::ostringstream& o, const HostShape& s, int id, int mode) {
     const char* need_u = mode <= 1 ? "true" : "(flags & 1)";
     o << "    if (" << need_u << ") {\n";
     for (int t = 0; t < k; ++t) {
-        o << "      { const int v = I->var[base + " << 32 * t << "]; " << nm("u", t) << " = I->T[v];";
+        o << "      { const int v = __ldcs(I->var + base + " << 32 * t << "); " << nm("u", t) << " = I->T[v];";
         if (mode <= 1) o << " if (local) ep_var[" << 32 * t << "] = v;";
         o << " }\n";
     }

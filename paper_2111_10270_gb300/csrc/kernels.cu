@@ -39,9 +39,8 @@ struct FlatArgs {
 // every warp slot busy).  Variables with one or two copies -- most of them --
 // read their slot positions from an 8-byte record, so their multipliers are
 // one dependent load away; longer lists continue in csr_pos.
-__global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= a.total) return;
+// one listed variable with at most 8 copies (work index g of the flat batch)
+__device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     if (FDOG_INACTIVE(I->ctl)) return;
@@ -64,6 +63,14 @@ __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
     for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
         if (q < cnt) s += l[q];
     I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
+}
+
+// Two variables per thread (one block covers 512 consecutive work entries),
+// so that each thread keeps two independent gather chains in flight.
+__global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
+    const int g0 = blockIdx.x * 512 + threadIdx.x;
+    if (g0 < a.total) reduce_T_one(a, g0);
+    if (g0 + 256 < a.total) reduce_T_one(a, g0 + 256);
 }
 
 // Variables with more than 8 copies (one assignment variable of a matching
@@ -625,7 +632,7 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
         cfg.count();
     }
     if (b.work_total > 0) {
-        reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
+        reduce_T_kernel<<<(b.work_total + 511) / 512, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
         cfg.count();
     }
     if (fork) {

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             if (valid) {
                 l = lam[base + static_cast<size_t>(t) * kTile];
                 if (need_t) {
-                    const int v = I->var[base + static_cast<size_t>(t) * kTile];
+                    const int v = __ldcs(I->var + base + static_cast<size_t>(t) * kTile);  // streamed once per pass
                     tb = I->T[v];
                     if (local) ep_var[t * kTile + lane] = v;
                 }
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
                 if (valid && t0 + c < k) {
                     const size_t p = base + static_cast<size_t>(t0 + c) * kTile;
                     L[c] = lam[p];
-                    if (with_var) V[c] = varp[p];
+                    if (with_var) V[c] = __ldcs(varp + p);  // streamed once per pass
                 }
             }
         };

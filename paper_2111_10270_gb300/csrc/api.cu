@@ -297,6 +297,10 @@ int release_device(fdog_instance* inst) {
     if (inst->arena) cudaFree(inst->arena);
     if (inst->dev.mm1) cudaFree(inst->dev.mm1);
     if (inst->host_ctl) cudaFreeHost(inst->host_ctl);
+    if (inst->solution_pinned && inst->host_x) {
+        inst->solution.assign(inst->host_x, inst->host_x + inst->n_vars);  // keep the last solution
+        inst->solution_pinned = false;
+    }
     if (inst->host_x) cudaFreeHost(inst->host_x);
     inst->prof.release();
     cudaGetLastError();
@@ -797,7 +801,7 @@ int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used) {
 int fdog_solution(fdog_instance* inst, uint8_t* x, double* objective, int32_t* feasible) {
     if (!inst) return FDOG_EINVAL;
     if (!inst->has_solution) return FDOG_ESTATE;
-    if (x) std::memcpy(x, inst->solution.data(), inst->solution.size());
+    if (x) std::memcpy(x, inst->solution_pinned ? inst->host_x : inst->solution.data(), static_cast<size_t>(inst->n_vars));
     if (objective) *objective = inst->objective;
     if (feasible) *feasible = inst->feasible;
     return FDOG_OK;

@@ -288,12 +288,21 @@ int finish_all(Engine& e, BatchView& v, const std::vector<int>& noconv) {
     if (rc != FDOG_OK) return rc;
     for (size_t i = 0; i < v.members.size(); ++i) {
         fdog_instance* m = v.members[i];
-        // variables in BDDs from the device; presolved and row-free ones from the plan
-        if (m->dec.n_bdds > 0) m->solution.assign(m->host_x, m->host_x + m->n_vars);
-        else m->solution.assign(static_cast<size_t>(m->n_vars), 0);
+        // variables in BDDs from the device (left in the pinned staging buffer
+        // until read or released); presolved and row-free ones from the plan
+        uint8_t* x;
+        if (m->dec.n_bdds > 0) {
+            m->solution.clear();
+            m->solution_pinned = true;
+            x = m->host_x;
+        } else {
+            m->solution.assign(static_cast<size_t>(m->n_vars), 0);
+            m->solution_pinned = false;
+            x = m->solution.data();
+        }
         for (const int32_t j : m->dec.outside) {
             const int8_t f = m->dec.fixed[j];
-            m->solution[j] = f == 2 ? (m->cost[j] < 0 ? 1 : 0) : static_cast<uint8_t>(f);
+            x[j] = f == 2 ? (m->cost[j] < 0 ? 1 : 0) : static_cast<uint8_t>(f);
         }
         m->objective = (m->dec.n_bdds > 0 ? st[i].objective : 0.0) + m->dec.const_obj;
         m->feasible = st[i].n_rejected == 0 ? 1 : 0;

@@ -72,6 +72,7 @@ struct fdog_instance {
     fdog::LaunchCfg cfg;
     fdog::InstCtl* host_ctl = nullptr;  // pinned
     uint8_t* host_x = nullptr;          // pinned staging of the rounded solution
+    bool solution_pinned = false;       // the last solution lives in host_x (else in `solution`)
     fdog::Profiler prof;
     fdog::JitKernels jit;     // shape-specialised kernels of this instance's shapes
     bool jit_failed = false;  // NVRTC unavailable or failed: generic kernels only

@@ -45,7 +45,7 @@ __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const InstDev* __restrict__ I = a.insts + ii;
     if (FDOG_INACTIVE(I->ctl)) return;
     const int w = g - __ldg(a.prefix + ii);  // below wb_start[FDOG_WBUCKETS - 1]: at most 8 copies
-    const int i = I->work[w];  // a variable with copies in several tiles
+    const int i = __ldcs(I->work + w);  // a variable with copies in several tiles (list streamed once)
     int b = 0;
 #pragma unroll
     for (int q = 1; q < FDOG_WBUCKETS - 1; ++q) b += w >= I->wb_start[q];
@@ -57,7 +57,7 @@ __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const float* __restrict__ lam = I->lam;
     float l[FDOG_WBUCKETS - 1];
 #pragma unroll
-    for (int q = 0; q < FDOG_WBUCKETS - 1; ++q) l[q] = q < cnt ? lam[pos[q * nb]] : 0.f;
+    for (int q = 0; q < FDOG_WBUCKETS - 1; ++q) l[q] = q < cnt ? lam[__ldcs(pos + q * nb)] : 0.f;
     float s = 0.f;
 #pragma unroll
     for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
@@ -65,12 +65,9 @@ __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
 }
 
-// Two variables per thread (one block covers 512 consecutive work entries),
-// so that each thread keeps two independent gather chains in flight.
 __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
-    const int g0 = blockIdx.x * 512 + threadIdx.x;
-    if (g0 < a.total) reduce_T_one(a, g0);
-    if (g0 + 256 < a.total) reduce_T_one(a, g0 + 256);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < a.total) reduce_T_one(a, g);
 }
 
 // Variables with more than 8 copies (one assignment variable of a matching
@@ -83,12 +80,12 @@ __global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     if (FDOG_INACTIVE(I->ctl)) return;
-    const int i = I->work[I->wb_start[FDOG_WBUCKETS - 1] + (g - __ldg(a.prefix + ii))];
+    const int i = __ldcs(I->work + I->wb_start[FDOG_WBUCKETS - 1] + (g - __ldg(a.prefix + ii)));
     const int b = I->csr_off[i], cnt = I->csr_off[i + 1] - b;
     const int32_t* __restrict__ pos = I->csr_pos + b;
     const float* __restrict__ lam = I->lam;
     float s = 0.f;
-    for (int q = lane; q < cnt; q += 32) s += lam[pos[q]];
+    for (int q = lane; q < cnt; q += 32) s += lam[__ldcs(pos + q)];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
@@ -632,7 +629,7 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
         cfg.count();
     }
     if (b.work_total > 0) {
-        reduce_T_kernel<<<(b.work_total + 511) / 512, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
+        reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
         cfg.count();
     }
     if (fork) {

@@ -59,6 +59,7 @@ def _load():
             "orc_energies": (i32, [P, ptr]),
             "orc_pass": (i32, [P, i32, f64, ptr]),
             "orc_iterate": (i32, [P, i32, f64, ptr]),
+            "orc_iterate_serial": (i32, [P, i32, ptr]),
             "orc_addback": (i32, [P, f64]),
             "orc_min_marginals": (i32, [P, ptr, ptr]),
             "orc_round": (i32, [P, f64, f64, f64, i32, i32, u64, ptr, ptr, ptr, ptr]),
@@ -214,6 +215,15 @@ class Problem:
         rc = self._lib.orc_iterate(self._h, k, omega, _p(tr))
         if rc != OK:
             raise OracleError(rc, "orc_iterate")
+        return tr[:k]
+
+    def iterate_serial(self, k: int):
+        """k iterations of the serial min-marginal averaging of Eq. 4 (ascending
+        then descending variable order); returns the bound after each."""
+        tr = np.zeros(max(k, 1))
+        rc = self._lib.orc_iterate_serial(self._h, k, _p(tr))
+        if rc != OK:
+            raise OracleError(rc, "orc_iterate_serial")
         return tr[:k]
 
     def addback(self, omega: float = 0.5):

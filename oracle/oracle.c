@@ -631,6 +631,78 @@ int orc_iterate(orc_problem *p, int k, double omega, double *lb_trace) {
     return ORC_OK;
 }
 
+/*
+ * The serial min-marginal averaging of Eq. 4 (the prior scheme the paper
+ * contrasts with Alg. 1): variables are visited one at a time, in ascending
+ * index order and then in descending order (one iteration); for variable i
+ * the min-marginal differences M_ij of all its copies are computed at the
+ * current multipliers (Eq. 6, from full shortest-path sweeps of each BDD) and
+ * every copy is set to lambda^j_i - M_ij + (1/|J_i|) sum_k M_ik, after which
+ * all copies share one difference and sum_j lambda^j_i is unchanged.  The
+ * state is the plain multipliers (lo = 0, no deferred differences).
+ * lb_trace[t] (may be NULL) gets sum_j E_j + constant after iteration t.
+ */
+int orc_iterate_serial(orc_problem *p, int k, double *lb_trace) {
+    if (k < 0) return ORC_EINVAL;
+    int64_t S = p->S;
+    int n = p->n;
+    /* plain multipliers; no deferred state */
+    for (int64_t s = 0; s < S; ++s) { p->hi[s] -= p->lo[s]; p->lo[s] = 0.0; }
+    for (int i = 0; i < n; ++i) { p->D0[i] = p->D1[i] = p->Db0[i] = p->Db1[i] = 0.0; }
+    p->spf_valid = p->spb_valid = 0;
+    /* copies of each variable (ascending slots) and the BDD of each slot */
+    int64_t *vs0 = calloc(n + 1, sizeof(int64_t));
+    int64_t *vsl = malloc(sizeof(int64_t) * (S ? S : 1));
+    int *sbdd = malloc(sizeof(int) * (S ? S : 1));
+    for (int64_t s = 0; s < S; ++s) vs0[p->svar[s] + 1]++;
+    for (int i = 0; i < n; ++i) vs0[i + 1] += vs0[i];
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) fill[i] = vs0[i];
+    for (int64_t s = 0; s < S; ++s) vsl[fill[p->svar[s]]++] = s;
+    for (int j = 0; j < p->m; ++j)
+        for (int t = 0; t < p->bdd[j].k; ++t) sbdd[p->slot0[j] + t] = j;
+    int64_t NN = max_nodes(p), K = max_layers(p);
+    double *f = malloc(sizeof(double) * NN), *g = malloc(sizeof(double) * NN);
+    double *w0 = calloc(K > 0 ? K : 1, sizeof(double)), *w1 = malloc(sizeof(double) * (K > 0 ? K : 1));
+    int cmax = 0;
+    for (int i = 0; i < n; ++i) if (vs0[i + 1] - vs0[i] > cmax) cmax = (int)(vs0[i + 1] - vs0[i]);
+    double *M = malloc(sizeof(double) * (cmax > 0 ? cmax : 1));
+    for (int it = 0; it < k; ++it) {
+        for (int dir = 0; dir < 2; ++dir) {
+            for (int q = 0; q < n; ++q) {
+                int i = dir == 0 ? q : n - 1 - q;
+                int c = (int)(vs0[i + 1] - vs0[i]);
+                if (c == 0) continue;
+                double sum = 0.0;
+                for (int r = 0; r < c; ++r) {
+                    int64_t s = vsl[vs0[i] + r];
+                    int j = sbdd[s];
+                    const bdd_t *b = &p->bdd[j];
+                    int64_t s0 = p->slot0[j];
+                    for (int t = 0; t < b->k; ++t) { w0[t] = 0.0; w1[t] = p->hi[s0 + t]; }
+                    sp_forward(b, w0, w1, f);
+                    sp_backward(b, w0, w1, g);
+                    double m0, m1;
+                    int t = (int)(s - s0);
+                    layer_min_marginals(b, t, f, g, w0[t], w1[t], &m0, &m1);
+                    M[r] = m1 - m0;
+                    sum += M[r];
+                }
+                double avg = sum / c;
+                for (int r = 0; r < c; ++r) p->hi[vsl[vs0[i] + r]] += avg - M[r];
+            }
+        }
+        if (lb_trace) {
+            double lb = p->const_lb;
+            double *scr = f;
+            for (int j = 0; j < p->m; ++j) lb += bdd_energy(p, j, p->lo + p->slot0[j], p->hi + p->slot0[j], scr);
+            lb_trace[it] = lb;
+        }
+    }
+    free(vs0); free(vsl); free(sbdd); free(fill); free(f); free(g); free(w0); free(w1); free(M);
+    return ORC_OK;
+}
+
 /* final step of Alg. 1: add the deferred differences back (averaged) */
 int orc_addback(orc_problem *p, double omega) {
     for (int64_t s = 0; s < p->S; ++s) {

@@ -476,6 +476,72 @@ def test_rounding_perturbation_worked_example(oracle_mod):
     assert checked > 0 and any(c and abs(q[i]) > 1.2 for i, c in enumerate(conflict))
 
 
+# ----------------------------------------------------------------------------
+# the serial min-marginal averaging of Eq. 4
+# ----------------------------------------------------------------------------
+def test_serial_averaging_worked_example(oracle_mod):
+    """One iteration of Eq. 4 by hand on x0 + x1 <= 1 (BDD 0) and x0 + x1 >= 1
+    (BDD 1), costs (2, -1), lambda = c / 2 initially.  Two-variable rows have
+    closed-form min-marginals: for <= 1, m1(x0) = l0, m0(x0) = min(0, l1); for
+    >= 1, m1(x0) = l0 + min(0, l1), m0(x0) = l1 (and symmetrically for x1).
+    Ascending x0: M = (1.5, 1.0), average 1.25 -> lambda_0 = (0.75, 1.25);
+    x1: M = (-0.5, -1.75), average -1.125 -> lambda_1 = (-1.125, 0.125);
+    descending x1: M = (-1.125, -1.125), no change; x0: M = (1.875, 1.125),
+    average 1.5 -> lambda_0 = (0.375, 1.625).  Bound -1.125 + 0.125 = -1 =
+    OPT.  All values are dyadic, so exact."""
+    rb = ilpgen._RowBuilder()
+    rb.add([0, 1], [1, 1], -1, 1)
+    rb.add([0, 1], [1, 1], 1, 1)
+    ilp = rb.finish(2, np.array([2.0, -1.0]), "serial-example")
+    p = oracle_mod.Problem.from_ilp(ilp)
+    tr = p.iterate_serial(1)
+    hi, lo, _, _ = p.state()
+    assert list(hi - lo) == [0.375, -1.125, 1.625, 0.125]
+    assert tr[0] == -1.0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_serial_averaging_invariants(oracle_mod, seed):
+    """Eq. 4 keeps sum_j lambda^j_i = c_i, never lowers the bound (block
+    coordinate ascent), stays below the brute-force optimum, and leaves the
+    copies of the last variable it visits (variable 0, at the end of the
+    descending sweep) with one common min-marginal difference."""
+    ilp = ilpgen.random_ilp(11, 8, 500 + seed, max_row=4, max_coef=2)
+    opt, _ = bf_optimum(ilp)
+    p = oracle_mod.Problem.from_ilp(ilp)
+    tr = p.iterate_serial(8)
+    assert np.all(np.diff(tr) >= -1e-9 * max(1.0, abs(tr[-1])))
+    assert tr[-1] <= opt + 1e-9
+    hi, lo, _, _ = p.state()
+    var = p.slot_vars()
+    s = np.bincount(var, hi - lo, minlength=ilp.n_vars)
+    inb = np.bincount(var, minlength=ilp.n_vars) > 0
+    assert np.allclose(s[inb], np.asarray(ilp.cost)[inb], atol=1e-12)
+    m0, m1 = p.min_marginals()
+    d0 = (m1 - m0)[var == 0]
+    if len(d0) > 1:
+        assert np.allclose(d0, d0[0], atol=1e-9 * max(1.0, np.abs(d0).max()))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_serial_averaging_chain_reaches_viterbi(oracle_mod, seed):
+    """On a chain MRF (a tree, tight local polytope) the serial scheme reaches
+    the Viterbi optimum computed by dynamic programming."""
+    W, L = 12, 4
+    g = ilpgen.mrf_grid(1, W, L, seed, potts_max=2.0)
+    un, wE = g.meta["unary"], g.meta["potts"]
+    best = un[0].copy()
+    for c in range(1, W):
+        pen = wE[c - 1] * (np.arange(L)[:, None] != np.arange(L)[None, :])
+        best = (best[:, None] + pen).min(0) + un[c]
+    viterbi = best.min()
+    p = oracle_mod.Problem.from_ilp(g)
+    tr = p.iterate_serial(60)
+    assert np.all(np.diff(tr) >= -1e-9 * max(1.0, abs(tr[-1])))
+    assert tr[-1] <= viterbi + 1e-9
+    assert tr[-1] >= viterbi - 1e-8
+
+
 def test_tiny_mrf_sizes_and_rounding(oracle_mod):
     g = ilpgen.mrf_grid(8, 8, 3, 0)
     p = oracle_mod.Problem.from_ilp(g)

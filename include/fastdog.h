@@ -79,6 +79,13 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *                              -1 = one CTA per group of tiles; 0 = chosen by
  *                              the autotuner (block_threads = 0) or one wave.
  *                              Results do not depend on either setting.
+ *   update = 0                 dual update: 0 = parallel deferred min-marginal
+ *                              averaging (Alg. 1, Eq. 5); 1 = the serial
+ *                              averaging of Eq. 4 (each variable's copies
+ *                              averaged at once, variables in ascending then
+ *                              descending order; omega unused), run level by
+ *                              level; instances with update = 1 are solved
+ *                              alone (not in a batch or server)
  *   jit = 0                    shape-specialised sweep kernels, compiled with
  *                              NVRTC for BDD shapes of width <= 4 and length
  *                              <= 16: 0 = for such shapes with at least 4096
@@ -104,7 +111,8 @@ typedef struct {
     int32_t jit;
     int32_t fuse;
     int32_t grid_waves;
-    int32_t reserved[4];
+    int32_t update;
+    int32_t reserved[3];
 } fdog_params;
 
 /* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */

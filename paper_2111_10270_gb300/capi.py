@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
         ("jit", ctypes.c_int32),
         ("fuse", ctypes.c_int32),
         ("grid_waves", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("update", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

@@ -80,6 +80,11 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * std::max<size_t>(d.local_ent.size(), 4)},
         {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * std::max<size_t>(d.work.size(), 1)},
         {reinterpret_cast<void**>(&a.wpos), sizeof(int32_t) * std::max<size_t>(d.wpos.size(), 1)},
+        {reinterpret_cast<void**>(&a.lab), sizeof(float) * static_cast<size_t>(std::max<int64_t>(d.lab_floats, 1))},
+        {reinterpret_cast<void**>(&a.lab_off), sizeof(int32_t) * std::max<size_t>(d.lab_off.size(), 1)},
+        {reinterpret_cast<void**>(&a.tile_of_row), sizeof(int32_t) * std::max<size_t>(d.tile_of_row.size(), 1)},
+        {reinterpret_cast<void**>(&a.lev_f), sizeof(int32_t) * std::max<size_t>(d.lev_f_vars.size(), 1)},
+        {reinterpret_cast<void**>(&a.lev_b), sizeof(int32_t) * std::max<size_t>(d.lev_b_vars.size(), 1)},
         {reinterpret_cast<void**>(&a.tile_lb), sizeof(float2) * sz(nt)},
         {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
         {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
@@ -120,6 +125,7 @@ int plan(fdog_instance* inst, bool compile_jit) {
             inst->last_error = "row longer than the shared-memory sweep kernels take";
             return FDOG_EUNSUPPORTED;
         }
+    if (inst->params.update == 1) build_serial_schedule(inst->n_vars, inst->dec);
     std::vector<int> ids = jit_ids(inst);
     if (compile_jit && !ids.empty()) {
         std::string why;
@@ -177,6 +183,9 @@ int allocate_and_upload(fdog_instance* inst) {
     h.local_ent = a.local_ent;
     h.work = a.work;
     h.wpos = a.wpos;
+    h.lab = a.lab;
+    h.lab_off = a.lab_off;
+    h.tile_of_row = a.tile_of_row;
     h.n_work = static_cast<int32_t>(d.work.size());
     for (int b = 0; b <= FDOG_WBUCKETS; ++b) h.wb_start[b] = d.wb_start[b];
     for (int b = 0; b < FDOG_WBUCKETS; ++b) h.wb_pos[b] = d.wb_pos[b];
@@ -256,6 +265,10 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
     up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());
     up(a.wpos, d.wpos.data(), sizeof(int32_t) * d.wpos.size());
+    up(a.lab_off, d.lab_off.data(), sizeof(int32_t) * d.lab_off.size());
+    up(a.tile_of_row, d.tile_of_row.data(), sizeof(int32_t) * d.tile_of_row.size());
+    up(a.lev_f, d.lev_f_vars.data(), sizeof(int32_t) * d.lev_f_vars.size());
+    up(a.lev_b, d.lev_b_vars.data(), sizeof(int32_t) * d.lev_b_vars.size());
     up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
     if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
     return FDOG_OK;
@@ -468,6 +481,7 @@ int fdog_params_default(fdog_params* p) {
     p->seed = 0;
     p->block_threads = 0;
     p->grid_waves = 0;
+    p->update = 0;
     return FDOG_OK;
 }
 
@@ -497,7 +511,8 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
     if (params) p = *params; else fdog_params_default(&p);
     if (!(p.omega > 0.0 && p.omega <= 1.0) || !(p.delta > 0.0) || !(p.alpha >= 1.0) || p.window < 1 ||
         p.window >= kLbRing || p.min_iters < 0 || p.rounding_dual_iters < 0 || p.max_rounds < 0 ||
-        p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0 || p.grid_waves < -1)
+        p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0 || p.grid_waves < -1 ||
+        p.update < 0 || p.update > 1)
         return FDOG_EINVAL;
     for (int32_t i = 0; i < n_vars; ++i)
         if (!std::isfinite(cost[i])) return FDOG_EINVAL;

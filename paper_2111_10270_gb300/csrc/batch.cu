@@ -31,6 +31,7 @@ int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream,
         if (insts[i]->device != dev) return FDOG_EINVAL;
         for (int32_t j = 0; j < i; ++j)
             if (insts[j] == insts[i]) return FDOG_EINVAL;  // an instance may appear once
+        if (n > 1 && insts[i]->params.update == 1) return FDOG_EUNSUPPORTED;  // the serial update runs alone
     }
     fdog_batch* b = new (std::nothrow) fdog_batch();
     if (!b) return FDOG_ENOMEM;

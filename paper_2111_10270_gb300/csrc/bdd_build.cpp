@@ -424,4 +424,51 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     return FDOG_OK;
 }
 
+void build_serial_schedule(int32_t n_vars, Decomposition& d) {
+    const int64_t rows = d.slots_pad / kTile;
+    d.tile_of_row.assign(static_cast<size_t>(rows), -1);
+    d.lab_off.resize(d.tiles.size());
+    int64_t off = 0;
+    for (size_t ti = 0; ti < d.tiles.size(); ++ti) {
+        const TileDev& t = d.tiles[ti];
+        const ShapeDev& sh = d.shape_dev[t.shape];
+        for (int l = 0; l < sh.k; ++l) d.tile_of_row[t.slot_base / kTile + l] = static_cast<int32_t>(ti);
+        d.lab_off[ti] = static_cast<int32_t>(off);
+        off += static_cast<int64_t>(sh.k + 1) * sh.width * kTile;
+    }
+    d.lab_floats = off;
+    // levels: predecessor / successor of a copy is the slot one layer up / down in its tile
+    auto layer_of = [&](int32_t p) {
+        const TileDev& t = d.tiles[d.tile_of_row[p / kTile]];
+        return std::make_pair(p / kTile - t.slot_base / kTile, d.shape_dev[t.shape].k);
+    };
+    auto levels = [&](bool ascending, std::vector<int32_t>& loff, std::vector<int32_t>& lvars) {
+        std::vector<int32_t> lev(n_vars, -1);
+        int32_t top = -1;
+        for (int32_t q = 0; q < n_vars; ++q) {
+            const int32_t i = ascending ? q : n_vars - 1 - q;
+            const int32_t b = d.csr_off[i], e = d.csr_off[i + 1];
+            if (b == e) continue;
+            int32_t l = 0;
+            for (int32_t r = b; r < e; ++r) {
+                const int32_t p = d.csr_pos[r];
+                const auto [t, k] = layer_of(p);
+                if (ascending ? t > 0 : t + 1 < k) l = std::max(l, lev[d.var[ascending ? p - kTile : p + kTile]] + 1);
+            }
+            lev[i] = l;
+            top = std::max(top, l);
+        }
+        loff.assign(static_cast<size_t>(top + 2), 0);
+        for (int32_t i = 0; i < n_vars; ++i)
+            if (lev[i] >= 0) loff[lev[i] + 1]++;
+        for (int32_t l = 0; l <= top; ++l) loff[l + 1] += loff[l];
+        lvars.resize(static_cast<size_t>(loff[top + 1]));
+        std::vector<int32_t> fill(loff.begin(), loff.end() - 1);
+        for (int32_t i = 0; i < n_vars; ++i)
+            if (lev[i] >= 0) lvars[fill[lev[i]]++] = i;
+    };
+    levels(true, d.lev_f_off, d.lev_f_vars);
+    levels(false, d.lev_b_off, d.lev_b_vars);
+}
+
 }  // namespace fdog

@@ -121,6 +121,22 @@ int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& membe
     prefix(&b.wide_prefix, &b.wide_total, [](fdog_instance* m) {
         return m->dec.wb_start[FDOG_WBUCKETS] - m->dec.wb_start[FDOG_WBUCKETS - 1];
     });
+    for (int i = 0; i < n; ++i) {
+        const fdog_instance* m = members[i];
+        if (m->params.update != 1) continue;
+        if (n > 1) {
+            e.err = "an instance with the serial update (update = 1) runs alone";
+            return FDOG_EUNSUPPORTED;
+        }
+        const Decomposition& d = m->dec;
+        b.serial.inst = reinterpret_cast<const InstDev*>(dbase);
+        b.serial.lev_f_off = d.lev_f_off.data();
+        b.serial.lev_b_off = d.lev_b_off.data();
+        b.serial.n_lev_f = d.lev_f_off.empty() ? 0 : static_cast<int>(d.lev_f_off.size()) - 1;
+        b.serial.n_lev_b = d.lev_b_off.empty() ? 0 : static_cast<int>(d.lev_b_off.size()) - 1;
+        b.serial.lev_f = m->dev.lev_f;
+        b.serial.lev_b = m->dev.lev_b;
+    }
     if (!ids.empty()) {
         // a server keeps one module for every shape it has seen, so that views
         // of changing member sets do not each need a compile

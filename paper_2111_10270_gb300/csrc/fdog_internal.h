@@ -121,6 +121,10 @@ struct InstDev {
     const uint16_t* local_ent;  // [4 per entry] copy offsets (32 t + lane) within the tile, ascending, 0xFFFF unused
     const int32_t* work;     // [n_work] variables the deferred-sum kernel handles (copies in several tiles),
                              //          grouped into buckets by copy count (FDOG_WBUCKETS)
+    float* lab;              // serial update (Eq. 4): per tile, labels of every layer [t][v][lane] then the
+                             // running labels [v][lane] of the sweep, at lab_off[tile]
+    const int32_t* lab_off;
+    const int32_t* tile_of_row;  // tile of each row of 32 padded slots
     const int32_t* wpos;     // slot positions of the bucketed variables: bucket b (count c = b + 1, nb
                              // variables) holds copy q of its j-th variable at wpos[wb_pos[b] + q nb + j]
     const double* cost;      // [n]
@@ -195,6 +199,12 @@ struct Decomposition {
     std::vector<uint16_t> local_ent;
     std::vector<int32_t> work;      // variables left to the deferred-sum kernel, bucketed by copy count
     std::vector<int32_t> wpos;      // bucketed slot positions (see InstDev::wpos)
+    // serial schedule (update = 1, Eq. 4); empty otherwise
+    std::vector<int32_t> tile_of_row;          // tile of each row of 32 padded slots
+    std::vector<int32_t> lab_off;              // per tile: first float of its label region
+    int64_t lab_floats = 0;                    // sum over tiles of (k + 1) * W * 32
+    std::vector<int32_t> lev_f_off, lev_f_vars;  // variables by level, ascending sweep
+    std::vector<int32_t> lev_b_off, lev_b_vars;  // descending sweep
     int32_t wb_start[FDOG_WBUCKETS + 1] = {0};
     int32_t wb_pos[FDOG_WBUCKETS] = {0};
     int64_t n_local_vars = 0;
@@ -214,6 +224,13 @@ struct Decomposition {
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
                         int jit_mode, bool fuse_local, Decomposition& out, std::string& err);
+
+// The schedule of the serial update (Eq. 4) on a built decomposition: a
+// variable's ascending level is one more than the largest level of the
+// variables before it in its BDDs (0 if it leads each of them), so variables
+// of one level share no BDD and visiting levels in order matches visiting
+// variables in ascending index order on every BDD; likewise descending.
+void build_serial_schedule(int32_t n_vars, Decomposition& d);
 
 // shape-specialised code (jit.cpp): process-wide shape registry and kernels
 int jit_register_shape(const HostShape& s);  // id of the shape's structure

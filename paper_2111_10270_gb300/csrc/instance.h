@@ -38,6 +38,11 @@ struct DevArrays {
     uint16_t* local_ent = nullptr;
     int32_t* work = nullptr;
     int32_t* wpos = nullptr;
+    float* lab = nullptr;            // serial update: labels of every layer and the running labels, per tile
+    int32_t* lab_off = nullptr;
+    int32_t* tile_of_row = nullptr;
+    int32_t* lev_f = nullptr;        // serial update: variables by level (ascending, descending sweeps)
+    int32_t* lev_b = nullptr;
     float2* tile_lb = nullptr;
     double* chunk_lb = nullptr;
     double* obj_chunk = nullptr;

@@ -761,7 +761,15 @@ cudaError_t launch_status(const DevBatch& b, InstStatus* dev_out, const LaunchCf
     return cudaGetLastError();
 }
 
+cudaError_t launch_lb_commit(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.n_inst == 0) return cudaSuccess;
+    cfg.count();
+    lb_commit_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    if (b.serial.inst) return launch_iteration_serial(b, cfg, s);
     cudaError_t e;
     if ((e = launch_sweep(b, kFwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
@@ -779,10 +787,7 @@ cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream
         if ((e = cudaEventRecord(cfg.side->join[1], cfg.side->s[1])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(s, cfg.side->join[1], 0)) != cudaSuccess) return e;
     }
-    if (b.n_inst == 0) return cudaSuccess;
-    cfg.count();
-    lb_commit_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst);
-    return cudaGetLastError();
+    return launch_lb_commit(b, cfg, s);
 }
 
 }  // namespace fdog

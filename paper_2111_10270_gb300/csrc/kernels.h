@@ -32,6 +32,21 @@ constexpr int kObjChunk = 8192;  // variables per block of the objective reducti
 // Device-side description of a batch of instances (one or many).  Work of
 // every kernel is a flat index space over all instances; prefix arrays map a
 // flat index back to (instance, local index).
+// Level schedule of the serial update (Eq. 4) for a view of one instance.
+struct SerialPlan {
+    const InstDev* inst = nullptr;       // device descriptor of the member; null: parallel update (Alg. 1)
+    const int32_t* lev_f_off = nullptr;  // host: first variable of each level, ascending sweep
+    const int32_t* lev_b_off = nullptr;  // host: descending sweep
+    int n_lev_f = 0, n_lev_b = 0;
+    const int32_t* lev_f = nullptr;      // device: variables by level
+    const int32_t* lev_b = nullptr;
+};
+
+struct FlatArgsS {
+    const InstDev* I;
+    int32_t total;
+};
+
 struct DevBatch {
     InstDev* insts = nullptr;
     int32_t* tile_prefix[kNumClasses] = {};  // [n_inst + 1] tiles of class c per instance
@@ -55,6 +70,7 @@ struct DevBatch {
     int32_t objchunks_total = 0;
     int32_t n_inst = 0;
     JitKernels jit;                          // kernels of the shape-specialised class
+    SerialPlan serial;                       // serial update only
 };
 
 
@@ -137,5 +153,9 @@ cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t 
 // one full dual iteration (forward pass, deferred sums, backward pass,
 // deferred sums, lower bound) on every instance of the batch
 cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+// one iteration of the serial update (Eq. 4) of a one-instance view (serial.cu)
+cudaError_t launch_iteration_serial(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
+// ring, iteration counter and stopping test of every member whose bound is staged
+cudaError_t launch_lb_commit(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 
 }  // namespace fdog

@@ -220,6 +220,10 @@ int fdog_server_create(int32_t device, int64_t hbm_budget, int32_t max_active, i
 int fdog_server_submit(fdog_server* s, fdog_instance* inst, uint64_t* ticket) {
     if (!s || !inst || !ticket) return FDOG_EINVAL;
     if (inst->built) return FDOG_ESTATE;
+    if (inst->params.update == 1) {
+        inst->last_error = "an instance with the serial update (update = 1) runs alone";
+        return FDOG_EUNSUPPORTED;
+    }
     // host work in the caller's thread: planning and the specialised kernels
     int rc = plan(inst, false);
     if (rc != FDOG_OK) return rc;

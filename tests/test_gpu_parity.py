@@ -215,6 +215,55 @@ def test_qap_and_cell_tracking_parity(P, oracle_mod, kind, jit):
     assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL, kp
 
 
+def serial_cases():
+    return {"mrf": ilpgen.mrf_grid(8, 8, 3, 2), "random": ilpgen.random_ilp(40, 30, 711, max_row=9, max_coef=3),
+            "cell": ilpgen.cell_tracking(12, 5, 20, 60), "qap": ilpgen.qap(11, 14, 28, 6, 3),
+            "long": long_narrow_rows()}
+
+
+@pytest.mark.parametrize("kind", ["mrf", "random", "cell", "qap", "long"])
+def test_serial_update_parity(P, oracle_mod, kind):
+    """The level-by-level serial update (update = 1) against the oracle's
+    Eq. 4, same iterations: bound after every iteration (relative to the sum
+    of the subproblem energies' magnitudes) and the final min-marginals."""
+    g = serial_cases()[kind]
+    iters = 15
+    inst = P.Instance.from_ilp(g, tol=0.0, update=1).build(0)
+    gl = np.array([inst.iterate(1)[1] for _ in range(iters)])
+    orc = oracle_mod.Problem.from_ilp(g)
+    ol, cond = [], []
+    for _ in range(iters):
+        ol.append(orc.iterate_serial(1)[0])
+        cond.append(np.abs(orc.energies()).sum())
+    bad = [t for t in range(iters) if not lb_close(gl[t], ol[t], scale=cond[t])]
+    assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    # every copy sum still equals the cost (Eq. 4 only redistributes)
+    _, _, lam = inst.multipliers()
+    sums = np.bincount(var, lam.astype(np.float64), minlength=g.n_vars)
+    inb = np.bincount(var, minlength=g.n_vars) > 0
+    assert np.abs(sums - np.asarray(g.cost))[inb].max() <= 1e-4 * max(1.0, np.abs(g.cost).max())
+
+
+def test_serial_update_runs_alone(P):
+    a = P.Instance.from_ilp(ilpgen.mrf_grid(6, 6, 3, 1), update=1).build(0)
+    b = P.Instance.from_ilp(ilpgen.mrf_grid(6, 6, 3, 2)).build(0)
+    with pytest.raises(P.FdogError):
+        P.Batch([a, b])
+    srv = P.Server(0)
+    with pytest.raises(P.FdogError):
+        srv.submit(P.Instance.from_ilp(ilpgen.mrf_grid(6, 6, 3, 3), update=1))
+    srv.close()
+    n, lb = a.iterate(30)
+    assert n == 30 or n > 0
+    rc, rounds = a.primal_round()
+    x, obj, feas = a.solution()
+    assert feas and obj >= lb - 1e-6 * max(1.0, abs(lb))
+
+
 def long_narrow_rows(seed=6):
     """Rows of width <= 4 and 9 .. 1000 layers: one-segment, multi-segment and
     ragged-segment shapes of the segmented kernels, some shapes filling more

@@ -69,6 +69,7 @@ def parse():
                     help="cell-tracking batch size for the batched-vs-sequential section (0: skip)")
     ap.add_argument("--serve-instances", type=int, default=48,
                     help="requests of the serving stream replayed in the serving section (0: skip)")
+    ap.add_argument("--schemes", type=int, default=1, help="update-scheme comparison section (0: skip)")
     ap.add_argument("--threads", type=int, default=min(16, os.cpu_count() or 1),
                     help="host threads / processes for instance generation and planning")
     return ap.parse_args()
@@ -380,6 +381,51 @@ def serving_section(torch, P, dev, stream, params, n_req, threads):
     }
 
 
+def update_scheme_section(P, dev, stream):
+    """Parallel deferred averaging (Alg. 1, Eq. 5) for several damping factors
+    against the serial averaging of Eq. 4, same instance, no early stop:
+    iterations each needs to come within 1e-3 / 1e-4 (relative) of the best
+    bound any of them reaches, and the device time per iteration."""
+    import ilpgen
+
+    cases = [("MRF grid 256x256, 4 labels, Potts U(0,2), seed 5", ilpgen.mrf_grid(256, 256, 4, 5, potts_max=2.0),
+              1500, 600),
+             ("cell-tracking instance (first of the seed-3 batch)", ilpgen.cell_tracking(ilpgen._child_seeds(3, 1)[0]),
+              1500, 300)]
+    schemes = [("parallel", 0.3), ("parallel", 0.5), ("parallel", 0.7), ("parallel", 1.0), ("serial", None)]
+    import torch
+
+    out = []
+    for name, g, it_par, it_ser in cases:
+        traces, per_iter = {}, {}
+        for kind, omega in schemes:
+            kw = dict(tol=0.0, update=1) if kind == "serial" else dict(tol=0.0, omega=omega)
+            inst = P.Instance.from_ilp(g, **kw).build(dev, stream)
+            iters = it_ser if kind == "serial" else it_par
+            tr = np.array([inst.iterate(1)[1] for _ in range(iters)])
+            inst.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            inst.iterate(iters)
+            torch.cuda.synchronize()
+            key = kind if kind == "serial" else f"parallel omega={omega}"
+            traces[key] = tr
+            per_iter[key] = (time.perf_counter() - t0) / iters * 1e3
+            inst.close()
+        best = max(float(t.max()) for t in traces.values())
+
+        def first(tr, gap):
+            hit = np.nonzero(tr >= best - gap * max(1.0, abs(best)))[0]
+            return int(hit[0]) + 1 if len(hit) else None
+
+        out.append({"instance": name, "best_bound": best,
+                    "schemes": {k: {"iters_to_1e-3": first(t, 1e-3), "iters_to_1e-4": first(t, 1e-4),
+                                    "final_bound": float(t[-1]), "ms_per_iter": per_iter[k],
+                                    "bound_non_decreasing": bool(np.all(np.diff(t) >= -1e-6 * max(1.0, abs(best))))}
+                                for k, t in traces.items()}})
+    return out
+
+
 def sweep_traffic():
     """DRAM bytes per update-sweep launch from the committed ncu summary, if
     the sweep's generator sources are unchanged since that capture."""
@@ -527,7 +573,9 @@ def main():
                          f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
 
     # ---- batched and served instance mixes (rank 0, N = 1) ---------------------
-    batched = served = None
+    batched = served = schemes = None
+    if rank == 0 and world == 1 and args.schemes:
+        schemes = update_scheme_section(P, dev, stream)
     if rank == 0 and world == 1 and args.batch_instances > 0:
         batched = batched_section(torch, P, dev, stream, params, args.batch_instances, args.threads)
     if rank == 0 and world == 1 and args.serve_instances > 0:
@@ -546,7 +594,7 @@ def main():
                               else f"inputs fit in L2 ({dev_bytes / 1e6:.0f} MB resident); no flush between steps"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "batched": batched, "serving": served,
+            "batched": batched, "serving": served, "update_schemes": schemes,
         }
         print(json.dumps(line), flush=True)
     inst.close()

@@ -39,6 +39,22 @@ __device__ __forceinline__ void fdog_tile_local_sums(const InstDev* __restrict__
     }
 }
 
+// L2 prefetch of the multiplier and variable rows of the tile this warp
+// visits next (lane t takes layer t), issued before the current tile is
+// computed so that the next tile's first loads hit L2.
+__device__ __forceinline__ void fdog_prefetch_tile(const SweepArgs& a, int g, int lane) {
+    if (g >= a.total) return;
+    const int ii = fdog_find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
+    const int k = I->shapes[tile.shape].k;
+    if (lane < k) {
+        const long long p = (long long)tile.slot_base + 32LL * lane;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(I->lam + p));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(I->var + p));
+    }
+}
+
 // MODE: 0 ascending pass with updates, 1 descending pass with updates,
 //       2 min-marginals, 3 energies only
 template <int MODE>
@@ -50,6 +66,7 @@ __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
     float* ep_lam = fdog_smem + (long long)wib * a.epi * 32 * 2;
     int* ep_var = (int*)(ep_lam + (long long)a.epi * 32);
     for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        fdog_prefetch_tile(a, g + gridDim.x * wpb, lane);
         const int ii = fdog_find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if (MODE <= 1 && FDOG_INACTIVE(I->ctl)) continue;

@@ -108,6 +108,22 @@ __device__ __forceinline__ void tile_local_sums(const InstDev* __restrict__ I, i
     }
 }
 
+// L2 prefetch of the multiplier and variable rows of the tile this warp
+// visits next (lane t takes layer t), issued before the current tile is
+// computed so that the next tile's first loads hit L2.
+__device__ __forceinline__ void prefetch_tile(const SweepArgs& a, int g, int lane) {
+    if (g >= a.total) return;
+    const int ii = find_inst(a.prefix, a.n_inst, g);
+    const InstDev* __restrict__ I = a.insts + ii;
+    const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
+    const int k = I->shapes[tile.shape].k;
+    for (int t = lane; t < k; t += kTile) {
+        const long long p = static_cast<long long>(tile.slot_base) + static_cast<long long>(kTile) * t;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(I->lam + p));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(I->var + p));
+    }
+}
+
 // Loops over layers.  With REG the trip count is the constant kRegK and the
 // loops unroll completely, so every index into Store is a compile-time
 // constant and the arrays stay in registers.
@@ -123,6 +139,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        prefetch_tile(a, g + gridDim.x * wpb, lane);
         const int ii = find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
@@ -349,6 +366,7 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
     float* ep_lam = wsm + static_cast<size_t>(a.kstride) * W * kTile;
     int* ep_var = reinterpret_cast<int*>(ep_lam + static_cast<size_t>(a.epi) * kTile);
     for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
+        prefetch_tile(a, g + gridDim.x * wpb, lane);
         const int ii = find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {

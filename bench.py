@@ -429,9 +429,11 @@ def update_scheme_section(P, dev, stream):
     return out
 
 
-def sweep_traffic():
-    """DRAM bytes per update-sweep launch from the committed ncu summary, if
-    the sweep's generator sources are unchanged since that capture."""
+def sweep_traffic(workload):
+    """DRAM bytes per update-sweep launch from the committed ncu summary (of
+    the 512x512 MRF), if the sweep's generator sources are unchanged since."""
+    if workload != "mrf512":
+        return None
     try:
         rec = {}
         with open(TRAFFIC_FILE) as f:
@@ -536,9 +538,11 @@ def main():
     peak_src = "measured" if peak else "fallback"
     if not peak:
         peak = 6800.0
-    roofline = {"bound": "hbm", "kernel": "fdog_jit_fwd / fdog_jit_bwd (shape-specialised update sweeps)",
+    kernel_name = ("fdog_jit_fwd / fdog_jit_bwd (shape-specialised update sweeps)" if kp["jit_tiles"] * 2 >= tiles
+                   else "update sweeps of the dominant kernel class")
+    roofline = {"bound": "hbm", "kernel": kernel_name,
                 "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": sweep_traffic(),
+                "frac": achieved / peak if achieved else None, "traffic": sweep_traffic(args.workload),
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": sweep_avg_s * 1e6,
                 "launches": prof["sweep_launches"],
                 "deferred_sum_kernel": {"avg_launch_us": reduce_avg_s * 1e6, "alg_bytes_per_launch": reduce_bytes,

@@ -6,6 +6,9 @@
 // share one shape (the MRF encodings have two signatures for millions of
 // rows).  Shapes are built once and instanced per row.
 #include <algorithm>
+#include <atomic>
+#include <new>
+#include <thread>
 #include <cstring>
 #include <map>
 #include <numeric>
@@ -17,6 +20,33 @@
 namespace fdog {
 
 namespace {
+
+// fn(begin, end) over [0, n) in contiguous chunks on up to 16 host threads.
+// Callers give each chunk independent work and combine any per-chunk results
+// in chunk order, so the plan does not depend on the thread count.
+template <class F>
+void parallel_chunks(int64_t n, F&& fn) {
+    const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
+    const int nt = static_cast<int>(std::min<int64_t>(hw, (n + 32767) / 32768));
+    if (nt <= 1) {
+        fn(int64_t(0), n);
+        return;
+    }
+    std::atomic<bool> failed{false};
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            try {
+                fn(n * t / nt, n * (t + 1) / nt);
+            } catch (...) {
+                failed = true;
+            }
+        });
+    for (auto& x : th) x.join();
+    if (failed) throw std::bad_alloc();
+}
+
 
 constexpr int64_t kMaxShapeNodes = 1 << 20;
 
@@ -168,21 +198,27 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
 
     // rows with non-zero entries sorted by variable (Alg. 1 visits I_j ascending)
     std::vector<int64_t> rb(n_rows + 1, 0);
-    std::vector<int32_t> rv;
-    std::vector<int64_t> ra;
-    rv.reserve(row_ptr[n_rows]);
-    ra.reserve(row_ptr[n_rows]);
-    {
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) {
+            int64_t c = 0;
+            for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q) c += coef[q] != 0;
+            rb[j + 1] = c;
+        }
+    });
+    for (int32_t j = 0; j < n_rows; ++j) rb[j + 1] += rb[j];
+    std::vector<int32_t> rv(static_cast<size_t>(rb[n_rows]));
+    std::vector<int64_t> ra(static_cast<size_t>(rb[n_rows]));
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
         std::vector<std::pair<int32_t, int32_t>> tmp;
-        for (int32_t j = 0; j < n_rows; ++j) {
+        for (int64_t j = j0; j < j1; ++j) {
             tmp.clear();
             for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q)
                 if (coef[q] != 0) tmp.emplace_back(col[q], coef[q]);
             if (!std::is_sorted(tmp.begin(), tmp.end())) std::sort(tmp.begin(), tmp.end());
-            for (auto& [c, v] : tmp) { rv.push_back(c); ra.push_back(v); }
-            rb[j + 1] = static_cast<int64_t>(rv.size());
+            int64_t o = rb[j];
+            for (auto& [c, v] : tmp) { rv[o] = c; ra[o] = v; ++o; }
         }
-    }
+    });
 
     std::unordered_map<std::string, int> cache;
     std::vector<Analysis> analyses;
@@ -264,9 +300,23 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         int sh = shape_of_an[id];
         bdds.push_back({out.shape_cls[sh], sh, j});
     }
-    std::stable_sort(bdds.begin(), bdds.end(), [](const Bdd& x, const Bdd& y) {
-        return x.cls != y.cls ? x.cls < y.cls : x.shape < y.shape;
-    });
+    {
+        // stable counting sort by (class, shape): BDDs keep row order within a shape
+        const int ns = static_cast<int>(out.shapes.size());
+        std::vector<int> order(ns);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+            return out.shape_cls[x] != out.shape_cls[y] ? out.shape_cls[x] < out.shape_cls[y] : x < y;
+        });
+        std::vector<int64_t> start(ns + 1, 0);
+        for (const Bdd& d : bdds) start[d.shape + 1]++;
+        std::vector<int64_t> at(ns, 0);
+        int64_t acc = 0;
+        for (int r = 0; r < ns; ++r) { at[order[r]] = acc; acc += start[order[r] + 1]; }
+        std::vector<Bdd> sorted(bdds.size());
+        for (const Bdd& d : bdds) sorted[at[d.shape]++] = d;
+        bdds.swap(sorted);
+    }
 
     // presolve constants
     std::vector<int32_t> cnt(n_vars, 0);
@@ -333,22 +383,25 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     out.bdd_slot0.resize(bdds.size());
     out.row_bdd.assign(n_rows, -1);
     out.n_bdds = static_cast<int64_t>(bdds.size());
-    for (const TileDev& t : out.tiles) {
-        for (int l = 0; l < t.n_valid; ++l) {
-            const Bdd& d = bdds[t.bdd_base + l];
-            out.bdd_row[t.bdd_base + l] = d.row;
-            out.bdd_shape[t.bdd_base + l] = d.shape;
-            out.bdd_slot0[t.bdd_base + l] = t.slot_base + l;
-            out.row_bdd[d.row] = t.bdd_base + l;
-            out.n_nodes += out.shapes[d.shape].lstart.back();
-            int layer = 0;
-            for (int64_t q = rb[d.row]; q < rb[d.row + 1]; ++q) {
-                if (out.fixed[rv[q]] != -1) continue;
-                out.var[t.slot_base + static_cast<int64_t>(layer) * kTile + l] = rv[q];
-                ++layer;
+    for (const Bdd& d : bdds) out.n_nodes += out.shapes[d.shape].lstart.back();
+    parallel_chunks(static_cast<int64_t>(out.tiles.size()), [&](int64_t t0, int64_t t1) {
+        for (int64_t ti = t0; ti < t1; ++ti) {
+            const TileDev& t = out.tiles[ti];
+            for (int l = 0; l < t.n_valid; ++l) {
+                const Bdd& d = bdds[t.bdd_base + l];
+                out.bdd_row[t.bdd_base + l] = d.row;
+                out.bdd_shape[t.bdd_base + l] = d.shape;
+                out.bdd_slot0[t.bdd_base + l] = t.slot_base + l;
+                out.row_bdd[d.row] = t.bdd_base + l;
+                int layer = 0;
+                for (int64_t q = rb[d.row]; q < rb[d.row + 1]; ++q) {
+                    if (out.fixed[rv[q]] != -1) continue;
+                    out.var[t.slot_base + static_cast<int64_t>(layer) * kTile + l] = rv[q];
+                    ++layer;
+                }
             }
         }
-    }
+    });
     // per-variable slot lists (ascending padded position: a fixed summation order)
     out.csr_off.assign(n_vars + 1, 0);
     for (int32_t i = 0; i < n_vars; ++i) out.csr_off[i + 1] = out.csr_off[i] + cnt[i];
@@ -364,23 +417,45 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     // one pattern.
     std::vector<uint8_t> local(n_vars, 0);
     if (fuse_local) {
-        std::unordered_map<std::string, int> pat_ids;
-        std::vector<uint16_t> ent;
-        for (size_t ti = 0; ti < out.tiles.size(); ++ti) {
-            TileDev& t = out.tiles[ti];
-            if (out.shapes[t.shape].k > kEpiMaxK) continue;  // the sweep stages at most kEpiMaxK layers
+        // per tile, in parallel: its local variables' copy offsets (a variable's
+        // first copy lies in exactly one tile, so each is marked by one tile)
+        const int64_t nt = static_cast<int64_t>(out.tiles.size());
+        std::vector<int64_t> ent_off(nt + 1, 0);
+        auto scan = [&](int64_t ti, uint16_t* dst) {
+            const TileDev& t = out.tiles[ti];
+            if (out.shapes[t.shape].k > kEpiMaxK) return int64_t(0);  // the sweep stages at most kEpiMaxK layers
             const int64_t lo = t.slot_base, hi = lo + static_cast<int64_t>(out.shapes[t.shape].k) * kTile;
-            ent.clear();
+            int64_t m = 0;
             for (int64_t p = lo; p < hi; ++p) {
                 const int32_t v = out.var[p];
                 if (v < 0) continue;
                 const int32_t b = out.csr_off[v], c = out.csr_off[v + 1] - b;
                 if (c > 4 || out.csr_pos[b] != p || out.csr_pos[b + c - 1] >= hi) continue;  // p is the first copy
-                for (int q = 0; q < 4; ++q)
-                    ent.push_back(q < c ? static_cast<uint16_t>(out.csr_pos[b + q] - lo) : uint16_t(0xFFFF));
-                local[v] = 1;
+                if (dst) {
+                    for (int q = 0; q < 4; ++q)
+                        dst[4 * m + q] = q < c ? static_cast<uint16_t>(out.csr_pos[b + q] - lo) : uint16_t(0xFFFF);
+                    local[v] = 1;
+                }
+                ++m;
             }
-            if (ent.empty()) continue;
+            return 4 * m;
+        };
+        parallel_chunks(nt, [&](int64_t t0, int64_t t1) {
+            for (int64_t ti = t0; ti < t1; ++ti) ent_off[ti + 1] = scan(ti, nullptr);
+        });
+        for (int64_t ti = 0; ti < nt; ++ti) ent_off[ti + 1] += ent_off[ti];
+        std::vector<uint16_t> ents(static_cast<size_t>(ent_off[nt]));
+        parallel_chunks(nt, [&](int64_t t0, int64_t t1) {
+            for (int64_t ti = t0; ti < t1; ++ti) scan(ti, ents.data() + ent_off[ti]);
+        });
+        // patterns in tile order (deduplicated)
+        std::unordered_map<std::string, int> pat_ids;
+        for (int64_t ti = 0; ti < nt; ++ti) {
+            TileDev& t = out.tiles[ti];
+            const uint16_t* e0 = ents.data() + ent_off[ti];
+            const int64_t ne = ent_off[ti + 1] - ent_off[ti];
+            if (ne == 0) continue;
+            std::vector<uint16_t> ent(e0, e0 + ne);
             std::string key(reinterpret_cast<const char*>(ent.data()), ent.size() * sizeof(uint16_t));
             auto it = pat_ids.find(key);
             if (it == pat_ids.end()) {

@@ -73,7 +73,9 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *                              guaranteed, Sec. 4)
  *   seed = 0                   seed of the counter-based perturbation draws
  *   block_threads = 0          threads per CTA for the sweep kernels;
- *                              0 = use the built-in autotuner
+ *                              0 = use the built-in autotuner (it also picks
+ *                              the grid mode and the dual iterations per
+ *                              CUDA-graph replay, about 1 ms of device work)
  *   grid_waves = 0             sweep grid size: k > 0 = at most k waves of
  *                              resident CTAs (grid-stride loop beyond),
  *                              -1 = one CTA per group of tiles; 0 = chosen by
@@ -318,8 +320,8 @@ int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* swee
  * max_iters iterations), then Alg. 2 -- and gets exactly the results it would
  * get alone (all reductions are per instance in a fixed order).  Iterations
  * run as CUDA-graph replays on cuda_stream when it is not NULL; the sweep
- * kernels' warps per block are autotuned at creation when the first member's
- * params.block_threads is 0.  Members stay owned by the caller and must
+ * kernels' warps per block, grid mode and iterations per replay are
+ * autotuned at creation when the first member's params.block_threads is 0.  Members stay owned by the caller and must
  * outlive the batch; an instance may belong to one batch call at a time.
  *
  * fdog_batch_solve: Alg. 1 then Alg. 2 for every member from its current

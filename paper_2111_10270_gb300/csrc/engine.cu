@@ -498,6 +498,13 @@ int view_autotune(Engine& e, BatchView& v, bool tune_grid) {
     cudaEventDestroy(z);
     e.cfg.warps_per_block = best;
     e.cfg.max_waves = best_waves;
+    // iterations per graph replay: about 1 ms of device work per replay (an
+    // iteration costs about two and a half sweeps), so that the status read
+    // after a replay stays a small fraction of it; results do not depend on it
+    const double iter_ms = 2.5 * best_ms / 3.0;
+    int chunk = 4;
+    while (chunk < 32 && chunk * iter_ms < 1.0) chunk *= 2;
+    e.chunk = chunk;
     return FDOG_OK;
 }
 

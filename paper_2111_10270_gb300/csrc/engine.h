@@ -43,7 +43,7 @@ struct Engine {
     cudaStream_t stream = nullptr;
     LaunchCfg cfg;
     Profiler* prof = nullptr;  // optional kernel timing (graphs are not used while it is on)
-    int chunk = 8;             // iterations per graph launch
+    int chunk = 8;             // iterations per graph launch (set by view_autotune)
     std::vector<int> jit_universe;  // if set: the shape ids every view's specialised module covers
     InstStatus* dev_status = nullptr;
     InstStatus* host_status = nullptr;  // pinned
@@ -90,7 +90,8 @@ int engine_step(Engine& e, std::vector<Member>& ms);
 
 // Picks the sweep kernels' warps per block and grid mode for this view by
 // timing min-marginal sweeps (they write only scratch, so the dual state is
-// untouched; results do not depend on either choice).
+// untouched), and the iterations per graph replay from the measured sweep
+// time; results depend on none of the three.
 int view_autotune(Engine& e, BatchView& v, bool tune_grid = true);
 
 // Alg. 2 for every member (which must have finished their dual phase):

@@ -524,13 +524,23 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
         }
         const int64_t nnz = row_ptr[n_rows];
         if (nnz > 0 && (!col || !coef)) return FDOG_EINVAL;
-        std::vector<int32_t> last(n_vars, -1);
-        for (int32_t j = 0; j < n_rows; ++j)
-            for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q) {
-                if (col[q] < 0 || col[q] >= n_vars) return FDOG_EINVAL;
-                if (last[col[q]] == j) return FDOG_EINVAL;  // repeated column in a row
-                last[col[q]] = j;
-            }
+        // columns in range and no column twice in a row, rows checked in parallel
+        std::atomic<bool> bad{false};
+        try {
+            parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+                std::vector<int32_t> cols;
+                for (int64_t j = j0; j < j1 && !bad; ++j) {
+                    cols.assign(col + row_ptr[j], col + row_ptr[j + 1]);
+                    for (int32_t c : cols)
+                        if (c < 0 || c >= n_vars) { bad = true; break; }
+                    std::sort(cols.begin(), cols.end());
+                    if (std::adjacent_find(cols.begin(), cols.end()) != cols.end()) bad = true;
+                }
+            });
+        } catch (...) {
+            return FDOG_ENOMEM;
+        }
+        if (bad) return FDOG_EINVAL;
     }
     fdog_instance* inst = new (std::nothrow) fdog_instance();
     if (!inst) return FDOG_ENOMEM;

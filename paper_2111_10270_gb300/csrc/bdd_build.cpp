@@ -21,31 +21,6 @@ namespace fdog {
 
 namespace {
 
-// fn(begin, end) over [0, n) in contiguous chunks on up to 16 host threads.
-// Callers give each chunk independent work and combine any per-chunk results
-// in chunk order, so the plan does not depend on the thread count.
-template <class F>
-void parallel_chunks(int64_t n, F&& fn) {
-    const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 16u));
-    const int nt = static_cast<int>(std::min<int64_t>(hw, (n + 32767) / 32768));
-    if (nt <= 1) {
-        fn(int64_t(0), n);
-        return;
-    }
-    std::atomic<bool> failed{false};
-    std::vector<std::thread> th;
-    th.reserve(nt);
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&, t] {
-            try {
-                fn(n * t / nt, n * (t + 1) / nt);
-            } catch (...) {
-                failed = true;
-            }
-        });
-    for (auto& x : th) x.join();
-    if (failed) throw std::bad_alloc();
-}
 
 
 constexpr int64_t kMaxShapeNodes = 1 << 20;

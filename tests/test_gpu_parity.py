@@ -487,6 +487,57 @@ def test_early_stopping_rule(P, oracle_mod):
 # ----------------------------------------------------------------------------
 # full-size workload (512 x 512 grid, 4 labels) in the benchmark's launch configuration
 # ----------------------------------------------------------------------------
+def test_qap_evaluation_parity_full_size(P, oracle_mod):
+    """The QAP-shaped workload at its full size (500 x 1000, 20 candidates,
+    10-NN products): after 25 iterations the oracle evaluates the GPU's
+    finalised multipliers (bound, every slot's min-marginals)."""
+    g = ilpgen.qap(2, 500, 1000, 20)
+    inst = gpu_instance(P, g)
+    info = inst.info()
+    assert (info["n_vars"], info["n_slots"]) == (1166481, 8115367)
+    n, _ = inst.iterate(25)
+    assert n == 25
+    inst.finalize()
+    var, row, lam = inst.multipliers()
+    orc = oracle_mod.Problem.from_ilp(g)
+    perm = slot_order(orc, var, row)
+    orc.set_state(lam[perm].astype(np.float64))
+    _, fea = inst.lower_bound()
+    _, ofea = orc.lower_bounds()
+    assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum()), (fea, ofea)
+    var2, row2, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm2 = slot_order(orc, var2, row2)
+    assert rel_err(m1[perm2] - m0[perm2], om1 - om0).max() <= MM_RTOL
+
+
+def test_cell_batch_members_parity_full_size(P, oracle_mod):
+    """The 64-instance cell-tracking batch at full size, solved as one batch
+    with the autotuned launch shape (dual phase to the stopping rule, no
+    rounding): three sampled members evaluated by the oracle at their final
+    multipliers (bound, every slot's min-marginals)."""
+    ilps = ilpgen.cell_tracking_batch(3, 64)
+    insts = [P.Instance.from_ilp(g, max_rounds=0).build(0) for g in ilps]
+    batch = P.Batch(insts)
+    iters, _, _ = batch.solve(500)
+    assert np.all(iters > 0)
+    for q in (0, 31, 63):
+        g, inst = ilps[q], insts[q]
+        inst.finalize()
+        var, row, lam = inst.multipliers()
+        orc = oracle_mod.Problem.from_ilp(g)
+        perm = slot_order(orc, var, row)
+        orc.set_state(lam[perm].astype(np.float64))
+        _, fea = inst.lower_bound()
+        _, ofea = orc.lower_bounds()
+        assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum()), (q, fea, ofea)
+        var2, row2, m0, m1 = inst.min_marginals()
+        om0, om1 = orc.min_marginals()
+        perm2 = slot_order(orc, var2, row2)
+        assert rel_err(m1[perm2] - m0[perm2], om1 - om0).max() <= MM_RTOL, q
+    batch.close()
+
+
 def test_large_mrf_evaluation_parity_full_size(P, oracle_mod):
     g = ilpgen.mrf_grid(512, 512, 4, 1, potts_max=2.0)
     inst = gpu_instance(P, g)

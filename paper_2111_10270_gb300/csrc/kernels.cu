@@ -218,9 +218,7 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
         neumaier(S, Cc, I->const_lb);
         const double lb = S + Cc;
         ctl->ticket = 0;
-        if (a.target == kLbIterate) {
-            commit_iteration(ctl, lb);
-        } else if (a.target == kLbStage) {
+        if (a.target == kLbStage) {
             ctl->lb_staged = lb;
             ctl->staged = 1;
         } else {

@@ -22,7 +22,6 @@ constexpr int kMMAddT = 1;   // evaluate at lambda + T (the add-back of Alg. 1)
 constexpr int kMMBoth = 2;   // write m0 and m1 (else M = m1 - m0 into mm0)
 
 // lower-bound reduction targets
-constexpr int kLbIterate = 0;  // running bound of an iteration: ring, counter, stopping rule
 constexpr int kLbEval = 1;     // evaluation: InstCtl::lb_eval
 constexpr int kLbStage = 2;    // bound of an iteration into InstCtl::lb_staged (committed later)
 

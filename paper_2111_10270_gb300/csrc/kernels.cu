@@ -8,11 +8,14 @@
 //     labels of the direction opposite to the pass are recomputed on chip at
 //     the start of each pass, so no per-node state ever goes to HBM; per-slot
 //     multipliers are the only state the sweeps stream.
-//   * deferred sums: one thread per variable sums its slots in a fixed order
-//     (deterministic; no floating-point atomics).
-//   * lower bound: FP32 per BDD, compensated FP32 within a warp, FP64
-//     Neumaier across tiles with a fixed chunking per instance, so the bound
-//     of an instance does not depend on what else is in the batch.
+//   * deferred sums: one thread per variable with at most 8 copies (slot
+//     positions bucketed by copy count, read column by column), one warp per
+//     variable with more; copies summed in a fixed order (deterministic; no
+//     floating-point atomics).
+//   * lower bound: FP32 per BDD, compensated FP32 pairs per tile and per chunk
+//     of tiles, FP64 Neumaier across chunks with a fixed chunking per
+//     instance, so the bound of an instance does not depend on what else is
+//     in the batch.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -35,10 +38,10 @@ struct FlatArgs {
 // T_i = (C_i - sum_j lambda^j_i) / |J_i|.  Right after a pass, Prop. 1 gives
 // sum_j lambda^j_i + omega sum_j M_ij = C_i, so T_i equals the averaged
 // deferred term omega / |J_i| sum_k Mbar_ik of Eq. 5.
-// One thread per variable (no grid-stride loop: the block scheduler keeps
-// every warp slot busy).  Variables with one or two copies -- most of them --
-// read their slot positions from an 8-byte record, so their multipliers are
-// one dependent load away; longer lists continue in csr_pos.
+// One thread per listed variable with at most 8 copies (no grid-stride loop:
+// the block scheduler keeps every warp slot busy); its slot positions come
+// from the bucket of its copy count, one coalesced column per copy, so all of
+// its multiplier gathers are issued together.
 // one listed variable with at most 8 copies (work index g of the flat batch)
 __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const int ii = find_inst(a.prefix, a.n_inst, g);

@@ -75,6 +75,21 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ranks(elapsed, work, device):
+    """Whole-job figures of N independent replicas: the slowest rank's timed
+    span and the work of all ranks (all-reduce MAX / SUM over the default
+    process group, on `device`)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([elapsed, work], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    tsum = t[1:].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -518,11 +533,7 @@ def main():
     dual_iters = sum(r["dual_iters"] for r in results)
     arcs = 4.0 * nodes * dual_iters
     if world > 1:
-        t = torch.tensor([elapsed, arcs], dtype=torch.float64, device=f"cuda:{dev}")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        elapsed, arcs = float(tmax[0]), float(t[1])
+        elapsed, arcs = aggregate_ranks(elapsed, arcs, f"cuda:{dev}")
     value = arcs / elapsed
 
     # ---- roofline of the dominant kernel (update sweep) ----------------------

@@ -98,6 +98,19 @@ typedef struct fdog_instance fdog_instance; /* opaque, library-owned */
  *                              in one tile of 32 BDDs are formed inside the
  *                              update sweep (same operations, same order);
  *                              -1 = leave every variable to the separate pass
+ *   planner = 0                where fdog_build_bdds builds the decomposition
+ *                              of an unplanned instance: 0 = on the device
+ *                              when the instance allows it (else the host),
+ *                              1 = on the host, 2 = on the device only
+ *                              (FDOG_EUNSUPPORTED otherwise).  The device
+ *                              builder takes instances whose rows need no
+ *                              presolve (no row forces a variable or accepts
+ *                              every assignment; rows non-empty, sorted,
+ *                              without zero coefficients), with at most 1024
+ *                              distinct row signatures (sense, right-hand
+ *                              side, coefficient sequence), at most 4096
+ *                              copies of any variable, and update = 0.  Both
+ *                              builders give the same plan.
  */
 typedef struct {
     double omega;
@@ -114,7 +127,8 @@ typedef struct {
     int32_t fuse;
     int32_t grid_waves;
     int32_t update;
-    int32_t reserved[3];
+    int32_t planner;
+    int32_t reserved[2];
 } fdog_params;
 
 /* Fill *p with the defaults above.  Returns FDOG_EINVAL if p is NULL. */
@@ -171,14 +185,41 @@ int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes,
                  int32_t* lo, int32_t* hi);
 
 /*
+ * How the plan was built: *on_device = 1 if by the device builder (see
+ * params.planner), *seconds = wall time of building the decomposition (BDDs,
+ * layout, slot lists; without the NVRTC compile).  Either pointer may be
+ * NULL.  FDOG_ESTATE if not planned.
+ */
+int fdog_plan_stats(fdog_instance* inst, int32_t* on_device, double* seconds);
+
+/*
+ * Fingerprints of a planned instance's decomposition, one FNV-1a 64-bit
+ * digest per part, written to digest[0..FDOG_PLAN_DIGESTS):
+ *   0 presolve (fixed flags, constants)   1 shapes and templates
+ *   2 tiles and class ranges              3 slot variables (var)
+ *   4 per-variable slot lists             5 tile-local patterns and entries
+ *   6 deferred-sum buckets (work, wpos)   7 BDD <-> row maps
+ *   8 counts (BDDs, slots, nodes, local and work variables)
+ * Two plans with equal digests lay out every device array identically.  For
+ * a plan built on the device the arrays are read back once (host copy kept).
+ * FDOG_ESTATE if not planned; FDOG_ECUDA if the read-back fails.
+ */
+#define FDOG_PLAN_DIGESTS 9
+int fdog_plan_digest(fdog_instance* inst, uint64_t* digest);
+
+/*
  * Build the decomposition and upload it to `device` on `cuda_stream`:
  * presolve (fix variables a row forces, drop rows every assignment
  * satisfies), one reduced ordered BDD per remaining row over its variables in
  * ascending index order (Def. 4; arcs leaving layer i carry lambda_i as in
  * Fig. 3), the node layout, and the initial multipliers
  * lambda^j_i = c_i / |J_i| with M-bar = 0 (Alg. 1 text).
+ * The decomposition of an unplanned instance is built on the device or the
+ * host as params.planner says.
  * Errors: FDOG_EINFEASIBLE (a row cannot be satisfied), FDOG_ENOMEM (host or
  * device memory, or a row whose BDD exceeds the node limit), FDOG_ECUDA,
+ * FDOG_EUNSUPPORTED (a BDD wider or longer than the sweep kernels take;
+ * planner = 2 and an instance the device builder does not take),
  * FDOG_ESTATE if already built.  After fdog_release the instance may be
  * built again (on any device and stream); its plan is reused.
  */

@@ -23,6 +23,7 @@ FDOG_ETIMEOUT = -6
 FDOG_ENOCONVERGE = -7
 FDOG_EUNSUPPORTED = -8
 FDOG_LE, FDOG_EQ, FDOG_GE = -1, 0, 1
+PLAN_DIGESTS = 9  # FDOG_PLAN_DIGESTS
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "_build", "libfastdog.so")
@@ -50,7 +51,8 @@ class Params(ctypes.Structure):
         ("fuse", ctypes.c_int32),
         ("grid_waves", ctypes.c_int32),
         ("update", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("planner", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -62,6 +64,8 @@ SIGNATURES = {
     "fdog_create": (ctypes.c_int, [_i32, _P, _i32, _P, _P, _P, _P, _P, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "fdog_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i64)]),
     "fdog_fixed_vars": (ctypes.c_int, [_P, _P]),
+    "fdog_plan_stats": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
+    "fdog_plan_digest": (ctypes.c_int, [_P, _P]),
     "fdog_kernel_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                         ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                         ctypes.c_char_p, _i32]),
@@ -209,6 +213,18 @@ class Instance:
                     "fdog_kernel_plan")
         return {"jit_shapes": js.value, "jit_tiles": jt.value, "static_tiles": st.value, "local_vars": lv.value,
                 "work_vars": wv.value, "work_slots": ws.value, "note": note.value.decode(errors="replace")}
+
+    def plan_stats(self):
+        """(built on the device?, seconds spent building the decomposition)"""
+        od, sec = _i32(), ctypes.c_double()
+        self._check(self._L.fdog_plan_stats(self._h, ctypes.byref(od), ctypes.byref(sec)), "fdog_plan_stats")
+        return bool(od.value), sec.value
+
+    def plan_digest(self):
+        """Per-part fingerprints of the decomposition (equal digests: equal device layout)."""
+        d = np.zeros(PLAN_DIGESTS, np.uint64)
+        self._check(self._L.fdog_plan_digest(self._h, _ptr(d)), "fdog_plan_digest")
+        return d
 
     def fixed_vars(self):
         f = np.zeros(self.n_vars, np.int8)

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -77,9 +78,9 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.csr_off), sizeof(int32_t) * static_cast<size_t>(n + 1)},
         {reinterpret_cast<void**>(&a.csr_pos), sizeof(int32_t) * sz(d.n_slots)},
         {reinterpret_cast<void**>(&a.patterns), sizeof(int32_t) * std::max<size_t>(d.patterns.size(), 2)},
-        {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * std::max<size_t>(d.local_ent.size(), 4)},
-        {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * std::max<size_t>(d.work.size(), 1)},
-        {reinterpret_cast<void**>(&a.wpos), sizeof(int32_t) * std::max<size_t>(d.wpos.size(), 1)},
+        {reinterpret_cast<void**>(&a.local_ent), sizeof(uint16_t) * static_cast<size_t>(std::max<int64_t>(d.n_local_ent, 4))},
+        {reinterpret_cast<void**>(&a.work), sizeof(int32_t) * sz(d.n_work)},
+        {reinterpret_cast<void**>(&a.wpos), sizeof(int32_t) * sz(d.n_wpos)},
         {reinterpret_cast<void**>(&a.lab), sizeof(float) * static_cast<size_t>(std::max<int64_t>(d.lab_floats, 1))},
         {reinterpret_cast<void**>(&a.lab_off), sizeof(int32_t) * std::max<size_t>(d.lab_off.size(), 1)},
         {reinterpret_cast<void**>(&a.tile_of_row), sizeof(int32_t) * std::max<size_t>(d.tile_of_row.size(), 1)},
@@ -106,8 +107,20 @@ std::vector<int> jit_ids(const fdog_instance* inst) {
     return ids;
 }
 
+// rows longer than the shared-memory sweep kernels take (either builder)
+static int check_layer_limits(fdog_instance* inst) {
+    for (int c = 0; c < kNumClasses; ++c)
+        if (!class_is_reg(c) && inst->dec.kmax[c] > smem_max_layers(class_width(c))) {
+            inst->last_error = "row longer than the shared-memory sweep kernels take";
+            return FDOG_EUNSUPPORTED;
+        }
+    return FDOG_OK;
+}
+
 int plan(fdog_instance* inst, bool compile_jit) {
     if (inst->planned) return FDOG_OK;
+    free_device_plan(inst->dec, inst->stream);
+    const auto t0 = std::chrono::steady_clock::now();
     int rc;
     try {
         rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
@@ -120,11 +133,9 @@ int plan(fdog_instance* inst, bool compile_jit) {
         rc = FDOG_EINVAL;
     }
     if (rc != FDOG_OK) return rc;
-    for (int c = 0; c < kNumClasses; ++c)
-        if (!class_is_reg(c) && inst->dec.kmax[c] > smem_max_layers(class_width(c))) {
-            inst->last_error = "row longer than the shared-memory sweep kernels take";
-            return FDOG_EUNSUPPORTED;
-        }
+    inst->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    inst->planned_on_device = false;
+    if ((rc = check_layer_limits(inst)) != FDOG_OK) return rc;
     if (inst->params.update == 1) build_serial_schedule(inst->n_vars, inst->dec);
     std::vector<int> ids = jit_ids(inst);
     if (compile_jit && !ids.empty()) {
@@ -137,6 +148,87 @@ int plan(fdog_instance* inst, bool compile_jit) {
         }
     }
     inst->planned = true;
+    return FDOG_OK;
+}
+
+// Planning at build time: the device builder where the instance allows it
+// (parallel update, planner != 1), else the host builder.  Both give the
+// same plan.
+static int plan_for_build(fdog_instance* inst) {
+    if (inst->planned) return FDOG_OK;
+    const int mode = inst->params.planner;
+    if (mode != 1 && inst->params.update == 0) {
+        int rc = plan_on_device(inst, inst->jit_failed ? -1 : inst->params.jit, inst->params.fuse >= 0);
+        if (rc == FDOG_OK) {
+            if ((rc = check_layer_limits(inst)) != FDOG_OK) {
+                free_device_plan(inst->dec, inst->stream);
+                return rc;
+            }
+            std::vector<int> ids = jit_ids(inst);
+            std::string why;
+            if (!ids.empty() && jit_compile(ids, why) != FDOG_OK) {
+                inst->jit_note = why;
+                inst->jit_failed = true;
+                free_device_plan(inst->dec, inst->stream);
+                return plan_for_build(inst);
+            }
+            inst->planned = true;
+            inst->planned_on_device = true;
+            return FDOG_OK;
+        }
+        if (rc != plan_leave_to_host()) return rc;
+    }
+    if (mode == 2) {
+        inst->last_error = "the device planner does not take this instance (presolve work, serial update, "
+                           "too many row signatures or copies)";
+        return FDOG_EUNSUPPORTED;
+    }
+    return plan(inst);
+}
+
+int ensure_host_plan(fdog_instance* inst) {
+    Decomposition& d = inst->dec;
+    if (!d.on_device) return FDOG_OK;
+    if (!inst->arena || !d.d_bdd_row) return FDOG_ESTATE;
+    DeviceGuard g(inst->device);
+    const int64_t n = inst->n_vars;
+    try {
+        d.var.resize(d.slots_pad);
+        d.csr_off.resize(n + 1);
+        d.csr_pos.resize(d.n_slots);
+        d.work.resize(d.n_work);
+        d.wpos.resize(d.n_wpos);
+        d.local_ent.resize(d.n_local_ent);
+        d.bdd_row.resize(d.n_bdds);
+    } catch (const std::bad_alloc&) {
+        return FDOG_ENOMEM;
+    }
+    cudaError_t e = cudaStreamSynchronize(inst->stream);
+    auto down = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes > 0 && e == cudaSuccess) e = copy_async(inst, dst, src, bytes, cudaMemcpyDeviceToHost);
+    };
+    const DevArrays& a = inst->dev;
+    down(d.var.data(), a.var, sizeof(int32_t) * d.var.size());
+    down(d.csr_off.data(), a.csr_off, sizeof(int32_t) * d.csr_off.size());
+    down(d.csr_pos.data(), a.csr_pos, sizeof(int32_t) * d.csr_pos.size());
+    down(d.work.data(), a.work, sizeof(int32_t) * d.work.size());
+    down(d.wpos.data(), a.wpos, sizeof(int32_t) * d.wpos.size());
+    down(d.local_ent.data(), a.local_ent, sizeof(uint16_t) * d.local_ent.size());
+    down(d.bdd_row.data(), d.d_bdd_row, sizeof(int32_t) * d.bdd_row.size());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(inst->stream);
+    if (e != cudaSuccess) return fail_cuda(inst, e, "plan download");
+    d.bdd_shape.resize(d.n_bdds);
+    d.bdd_slot0.resize(d.n_bdds);
+    d.row_bdd.assign(inst->n_rows, -1);
+    for (const TileDev& t : d.tiles)
+        for (int l = 0; l < t.n_valid; ++l) {
+            const int32_t b = t.bdd_base + l;
+            d.bdd_shape[b] = t.shape;
+            d.bdd_slot0[b] = t.slot_base + l;
+            d.row_bdd[d.bdd_row[b]] = b;
+        }
+    free_device_plan(d, inst->stream);
+    d.on_device = false;
     return FDOG_OK;
 }
 
@@ -186,7 +278,7 @@ int allocate_and_upload(fdog_instance* inst) {
     h.lab = a.lab;
     h.lab_off = a.lab_off;
     h.tile_of_row = a.tile_of_row;
-    h.n_work = static_cast<int32_t>(d.work.size());
+    h.n_work = static_cast<int32_t>(d.n_work);
     for (int b = 0; b <= FDOG_WBUCKETS; ++b) h.wb_start[b] = d.wb_start[b];
     for (int b = 0; b < FDOG_WBUCKETS; ++b) h.wb_pos[b] = d.wb_pos[b];
     h.cost = a.cost;
@@ -257,14 +349,31 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.tiles, d.tiles.data(), sizeof(TileDev) * nt);
     up(a.shapes, d.shape_dev.data(), sizeof(ShapeDev) * d.shape_dev.size());
     up(a.tpl, d.tpl.data(), sizeof(uint16_t) * d.tpl.size());
-    up(a.var, d.var.data(), sizeof(int32_t) * S);
     up(a.cost, inst->cost.data(), sizeof(double) * n);
-    up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
-    up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
     up(a.patterns, d.patterns.data(), sizeof(int32_t) * d.patterns.size());
-    up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
-    up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());
-    up(a.wpos, d.wpos.data(), sizeof(int32_t) * d.wpos.size());
+    if (d.on_device) {
+        // arrays of a device-built plan: into the arena, then their buffers are released
+        auto d2d = [&](void* dst, const void* src, int64_t bytes) {
+            if (bytes > 0 && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, inst->stream);
+        };
+        d2d(a.var, d.d_var, sizeof(int32_t) * S);
+        d2d(a.csr_off, d.d_csr_off, sizeof(int32_t) * (n + 1));
+        d2d(a.csr_pos, d.d_csr_pos, sizeof(int32_t) * d.n_slots);
+        d2d(a.local_ent, d.d_local_ent, sizeof(uint16_t) * d.n_local_ent);
+        d2d(a.work, d.d_work, sizeof(int32_t) * d.n_work);
+        d2d(a.wpos, d.d_wpos, sizeof(int32_t) * d.n_wpos);
+        int32_t* keep = d.d_bdd_row;
+        d.d_bdd_row = nullptr;
+        free_device_plan(d, inst->stream);
+        d.d_bdd_row = keep;
+    } else {
+        up(a.var, d.var.data(), sizeof(int32_t) * S);
+        up(a.csr_off, d.csr_off.data(), sizeof(int32_t) * (n + 1));
+        up(a.csr_pos, d.csr_pos.data(), sizeof(int32_t) * d.n_slots);
+        up(a.local_ent, d.local_ent.data(), sizeof(uint16_t) * d.local_ent.size());
+        up(a.work, d.work.data(), sizeof(int32_t) * d.work.size());
+        up(a.wpos, d.wpos.data(), sizeof(int32_t) * d.wpos.size());
+    }
     up(a.lab_off, d.lab_off.data(), sizeof(int32_t) * d.lab_off.size());
     up(a.tile_of_row, d.tile_of_row.data(), sizeof(int32_t) * d.tile_of_row.size());
     up(a.lev_f, d.lev_f_vars.data(), sizeof(int32_t) * d.lev_f_vars.size());
@@ -303,6 +412,8 @@ int release_device(fdog_instance* inst) {
     if (!inst->built) return FDOG_OK;
     DeviceGuard g(inst->device);
     cudaStreamSynchronize(inst->stream);
+    int rc = ensure_host_plan(inst);  // the plan stays on the host for a later build
+    if (rc != FDOG_OK) return rc;
     delete inst->self_view;
     inst->self_view = nullptr;
     delete inst->engine;
@@ -414,7 +525,7 @@ int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool 
     DeviceGuard g(device);
     inst->device = device;
     inst->stream = static_cast<cudaStream_t>(cuda_stream);
-    int rc = plan(inst);
+    int rc = plan_for_build(inst);
     if (rc != FDOG_OK) return rc;
     const std::vector<int> ids = jit_ids(inst);
     if (!ids.empty()) {
@@ -424,7 +535,8 @@ int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool 
             inst->jit_note = why;
             inst->jit_failed = true;
             inst->planned = false;
-            if ((rc = plan(inst)) != FDOG_OK) return rc;
+            free_device_plan(inst->dec, inst->stream);
+            if ((rc = plan_for_build(inst)) != FDOG_OK) return rc;
         }
     }
     cudaDeviceProp prop;
@@ -482,6 +594,7 @@ int fdog_params_default(fdog_params* p) {
     p->block_threads = 0;
     p->grid_waves = 0;
     p->update = 0;
+    p->planner = 0;
     return FDOG_OK;
 }
 
@@ -512,7 +625,7 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
     if (!(p.omega > 0.0 && p.omega <= 1.0) || !(p.delta > 0.0) || !(p.alpha >= 1.0) || p.window < 1 ||
         p.window >= kLbRing || p.min_iters < 0 || p.rounding_dual_iters < 0 || p.max_rounds < 0 ||
         p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0 || p.grid_waves < -1 ||
-        p.update < 0 || p.update > 1)
+        p.update < 0 || p.update > 1 || p.planner < 0 || p.planner > 2)
         return FDOG_EINVAL;
     for (int32_t i = 0; i < n_vars; ++i)
         if (!std::isfinite(cost[i])) return FDOG_EINVAL;
@@ -585,7 +698,7 @@ int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tile
     if (!inst->planned) return FDOG_ESTATE;
     const Decomposition& d = inst->dec;
     if (local_vars) *local_vars = d.n_local_vars;
-    if (work_vars) *work_vars = static_cast<int64_t>(d.work.size());
+    if (work_vars) *work_vars = d.n_work;
     if (work_slots) *work_slots = d.n_work_slots;
     if (jit_shapes) *jit_shapes = static_cast<int32_t>(jit_ids(inst).size());
     const int64_t jt = d.cls_tile_begin[kJitClass + 1] - d.cls_tile_begin[kJitClass];
@@ -600,6 +713,62 @@ int fdog_kernel_plan(fdog_instance* inst, int32_t* jit_shapes, int64_t* jit_tile
     return FDOG_OK;
 }
 
+int fdog_plan_stats(fdog_instance* inst, int32_t* on_device, double* seconds) {
+    if (!inst) return FDOG_EINVAL;
+    if (!inst->planned) return FDOG_ESTATE;
+    if (on_device) *on_device = inst->planned_on_device ? 1 : 0;
+    if (seconds) *seconds = inst->plan_seconds;
+    return FDOG_OK;
+}
+
+int fdog_plan_digest(fdog_instance* inst, uint64_t* digest) {
+    if (!inst || !digest) return FDOG_EINVAL;
+    if (!inst->planned) return FDOG_ESTATE;
+    int rc = ensure_host_plan(inst);
+    if (rc != FDOG_OK) return rc;
+    const Decomposition& d = inst->dec;
+    auto fnv = [](uint64_t h, const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t q = 0; q < n; ++q) { h ^= c[q]; h *= 0x100000001B3ull; }
+        return h;
+    };
+    auto vec = [&](uint64_t h, const auto& v) {
+        const uint64_t n = v.size();
+        return fnv(fnv(h, &n, sizeof(n)), v.data(), v.size() * sizeof(v[0]));
+    };
+    auto val = [&](uint64_t h, const auto& x) { return fnv(h, &x, sizeof(x)); };
+    const uint64_t h0 = 0xCBF29CE484222325ull;
+    uint64_t h = h0;
+    h = vec(h, d.fixed);
+    h = vec(h, d.outside);
+    h = val(val(h, d.const_lb), d.const_obj);
+    digest[0] = h;
+    h = h0;
+    for (size_t s = 0; s < d.shapes.size(); ++s) {
+        const HostShape& sh = d.shapes[s];
+        h = val(val(h, sh.k), sh.width);
+        h = vec(vec(vec(h, sh.lstart), sh.lo), sh.hi);
+    }
+    h = vec(h, d.shape_cls);
+    h = vec(h, d.shape_dev);
+    digest[1] = vec(h, d.tpl);
+    h = vec(h0, d.tiles);
+    h = vec(h, d.cls_tile_begin);
+    h = fnv(h, d.kmax, sizeof(d.kmax));
+    digest[2] = fnv(h, d.cls_has_local, sizeof(d.cls_has_local));
+    digest[3] = vec(h0, d.var);
+    digest[4] = vec(vec(h0, d.csr_off), d.csr_pos);
+    digest[5] = vec(vec(h0, d.patterns), d.local_ent);
+    h = vec(vec(h0, d.work), d.wpos);
+    h = fnv(h, d.wb_start, sizeof(d.wb_start));
+    digest[6] = fnv(h, d.wb_pos, sizeof(d.wb_pos));
+    digest[7] = vec(vec(vec(vec(h0, d.bdd_row), d.bdd_shape), d.bdd_slot0), d.row_bdd);
+    h = val(val(val(val(h0, d.n_bdds), d.n_slots), d.n_nodes), d.slots_pad);
+    h = val(val(val(h, d.n_local_vars), d.n_work_slots), d.n_work_overflow);
+    digest[8] = val(val(val(h, d.n_work), d.n_wpos), d.n_local_ent);
+    return FDOG_OK;
+}
+
 int fdog_fixed_vars(fdog_instance* inst, int8_t* fixed) {
     if (!inst || !fixed) return FDOG_EINVAL;
     if (!inst->planned) return FDOG_ESTATE;
@@ -611,6 +780,8 @@ int fdog_row_bdd(fdog_instance* inst, int32_t row, int32_t* k, int32_t* n_nodes,
                  int32_t* lo, int32_t* hi) {
     if (!inst || !k || !n_nodes || row < 0 || row >= inst->n_rows) return FDOG_EINVAL;
     if (!inst->planned) return FDOG_ESTATE;
+    int rc = ensure_host_plan(inst);
+    if (rc != FDOG_OK) return rc;
     const Decomposition& d = inst->dec;
     const int32_t b = d.row_bdd[row];
     if (b < 0) { *k = 0; *n_nodes = 0; return FDOG_OK; }
@@ -744,6 +915,8 @@ static int slot_table(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32
     const Decomposition& d = inst->dec;
     if (!var) { *n_slots = d.n_slots; return FDOG_OK; }
     if (*n_slots < d.n_slots) return FDOG_EINVAL;
+    int rc = ensure_host_plan(inst);
+    if (rc != FDOG_OK) return rc;
     int64_t q = 0;
     for (const TileDev& t : d.tiles) {
         const int k = d.shapes[t.shape].k;
@@ -856,9 +1029,16 @@ int fdog_release(fdog_instance* inst) {
 
 void fdog_destroy(fdog_instance* inst) {
     if (!inst) return;
-    if (inst->built || inst->arena || inst->host_ctl) {
+    const Decomposition& d = inst->dec;
+    const bool device_plan = d.d_var || d.d_csr_off || d.d_csr_pos || d.d_work || d.d_wpos || d.d_local_ent ||
+                             d.d_bdd_row;
+    if (inst->built || inst->arena || inst->host_ctl || device_plan) {
         DeviceGuard g(inst->device);
         if (inst->stream || inst->arena) cudaStreamSynchronize(inst->stream);
+        if (device_plan) {
+            free_device_plan(inst->dec, inst->stream);
+            cudaStreamSynchronize(inst->stream);
+        }
         if (inst->arena) cudaFree(inst->arena);
         if (inst->dev.mm1) cudaFree(inst->dev.mm1);
         if (inst->host_ctl) cudaFreeHost(inst->host_ctl);

@@ -165,6 +165,49 @@ std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) 
 
 }  // namespace
 
+int analyse_row(const std::vector<int64_t>& a, int8_t sense, int64_t rhs, HostShape& shape, bool& presolve) {
+    Analysis an = analyse(a, sense, rhs);
+    if (an.status != FDOG_OK) return an.status;
+    presolve = an.full_cube;
+    for (int8_t f : an.forced) presolve = presolve || f >= 0;
+    shape = std::move(an.shape);
+    return FDOG_OK;
+}
+
+int shape_class(const HostShape& s, int jit_mode, int64_t n_bdds) {
+    int cls = class_of(s.width, s.k);
+    // a specialised kernel costs a compile; rare shapes stay generic in the default mode
+    const bool often = jit_mode >= 1 || n_bdds >= kJitMinBdds;
+    if (jit_mode >= 0 && often && s.width <= kJitMaxW && s.k <= kJitMaxK) cls = kJitClass;
+    if (cls < 0 || (!class_is_reg(cls) && s.k > (class_is_seg(cls) ? kMaxLayersSeg : kMaxLayersSmem))) return -1;
+    return cls;
+}
+
+void build_templates(Decomposition& out) {
+    out.shape_dev.resize(out.shapes.size());
+    for (size_t s = 0; s < out.shapes.size(); ++s) {
+        const HostShape& h = out.shapes[s];
+        int W = class_width(out.shape_cls[s]);
+        while (out.tpl.size() % 8) out.tpl.push_back(0);  // 16-byte aligned vector loads
+        const int jit = out.shape_cls[s] == kJitClass ? jit_register_shape(h) : -1;
+        ShapeDev d{h.k, static_cast<int32_t>(out.tpl.size()), W, jit};
+        out.shape_dev[s] = d;
+        for (int t = 0; t < h.k; ++t) {
+            int b = h.lstart[t], e = h.lstart[t + 1];
+            int nb = (t + 1 < h.k) ? h.lstart[t + 1] : 0;
+            for (int v = 0; v < W; ++v) {
+                uint8_t lo = kCodeBot, hi = kCodeBot;
+                if (b + v < e) {
+                    int l = h.lo[b + v], u = h.hi[b + v];
+                    lo = l == kArcTop ? kCodeTop : (l == kArcBot ? kCodeBot : static_cast<uint8_t>(l - nb));
+                    hi = u == kArcTop ? kCodeTop : (u == kArcBot ? kCodeBot : static_cast<uint8_t>(u - nb));
+                }
+                out.tpl.push_back(static_cast<uint16_t>(lo | (hi << 8)));
+            }
+        }
+    }
+}
+
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
                         int jit_mode, bool fuse_local, Decomposition& out, std::string& err) {
@@ -259,11 +302,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         int id = row_an[j];
         if (shape_of_an[id] < 0) {
             const HostShape& s = analyses[id].shape;
-            int cls = class_of(s.width, s.k);
-            // a specialised kernel costs a compile; rare shapes stay generic in the default mode
-            const bool often = jit_mode >= 1 || an_count[id] >= kJitMinBdds;
-            if (jit_mode >= 0 && often && s.width <= kJitMaxW && s.k <= kJitMaxK) cls = kJitClass;
-            if (cls < 0 || (!class_is_reg(cls) && s.k > (class_is_seg(cls) ? kMaxLayersSeg : kMaxLayersSmem))) {
+            const int cls = shape_class(s, jit_mode, an_count[id]);
+            if (cls < 0) {
                 err = "row " + std::to_string(j) + ": BDD width " + std::to_string(s.width) + " / length " +
                       std::to_string(s.k) + " exceeds the sweep kernels' limits";
                 return FDOG_EUNSUPPORTED;
@@ -309,29 +349,7 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     }
     out.const_obj = out.const_lb;
 
-    // templates
-    out.shape_dev.resize(out.shapes.size());
-    for (size_t s = 0; s < out.shapes.size(); ++s) {
-        const HostShape& h = out.shapes[s];
-        int W = class_width(out.shape_cls[s]);
-        while (out.tpl.size() % 8) out.tpl.push_back(0);  // 16-byte aligned vector loads
-        const int jit = out.shape_cls[s] == kJitClass ? jit_register_shape(h) : -1;
-        ShapeDev d{h.k, static_cast<int32_t>(out.tpl.size()), W, jit};
-        out.shape_dev[s] = d;
-        for (int t = 0; t < h.k; ++t) {
-            int b = h.lstart[t], e = h.lstart[t + 1];
-            int nb = (t + 1 < h.k) ? h.lstart[t + 1] : 0;
-            for (int v = 0; v < W; ++v) {
-                uint8_t lo = kCodeBot, hi = kCodeBot;
-                if (b + v < e) {
-                    int l = h.lo[b + v], u = h.hi[b + v];
-                    lo = l == kArcTop ? kCodeTop : (l == kArcBot ? kCodeBot : static_cast<uint8_t>(l - nb));
-                    hi = u == kArcTop ? kCodeTop : (u == kArcBot ? kCodeBot : static_cast<uint8_t>(u - nb));
-                }
-                out.tpl.push_back(static_cast<uint16_t>(lo | (hi << 8)));
-            }
-        }
-    }
+    build_templates(out);
 
     // tiles: runs of equal shape, kTile BDDs each, grouped by kernel class
     out.cls_tile_begin.assign(kNumClasses + 1, 0);
@@ -471,6 +489,9 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
                 out.wpos[out.wb_pos[b] + q * nb + j] = out.csr_pos[out.csr_off[bucket[b][j]] + q];
     }
     out.wb_start[FDOG_WBUCKETS] = static_cast<int32_t>(out.work.size());
+    out.n_work = static_cast<int64_t>(out.work.size());
+    out.n_wpos = static_cast<int64_t>(out.wpos.size());
+    out.n_local_ent = static_cast<int64_t>(out.local_ent.size());
     return FDOG_OK;
 }
 

@@ -218,7 +218,21 @@ struct Decomposition {
     std::vector<ShapeDev> shape_dev;
     std::vector<uint16_t> tpl;
     int64_t n_bdds = 0, n_slots = 0, n_nodes = 0, slots_pad = 0;
+    int64_t n_work = 0, n_wpos = 0, n_local_ent = 0;  // sizes of work, wpos, local_ent
     int kmax[kNumClasses] = {0};
+    // Plan built on the device: var, csr_off, csr_pos, work, wpos, local_ent
+    // and bdd_row exist only in device memory (d_* until the instance's arena
+    // takes the first six; bdd_row stays in d_bdd_row) until a host consumer
+    // downloads them; bdd_shape, bdd_slot0 and row_bdd are then derived from
+    // tiles and bdd_row.
+    bool on_device = false;
+    int32_t* d_var = nullptr;
+    int32_t* d_csr_off = nullptr;
+    int32_t* d_csr_pos = nullptr;
+    int32_t* d_work = nullptr;
+    int32_t* d_wpos = nullptr;
+    uint16_t* d_local_ent = nullptr;
+    int32_t* d_bdd_row = nullptr;
 };
 
 // fn(begin, end) over [0, n) in contiguous chunks on up to 16 host threads.
@@ -273,6 +287,15 @@ int jit_compile(const std::vector<int>& ids, std::string& err);
 int jit_kernels(const std::vector<int>& ids, JitKernels& out, std::string& err);
 // the generated CUDA source of the module (for inspection)
 std::string jit_source(const std::vector<int>& ids);
+
+// The BDD of one row (coefficients of its non-zero entries in ascending
+// variable order, no variable fixed); `presolve` is set when the row forces
+// some variable or accepts every assignment (the host presolve then has work).
+int analyse_row(const std::vector<int64_t>& a, int8_t sense, int64_t rhs, HostShape& shape, bool& presolve);
+// kernel class of a shape with n_bdds BDDs under a jit mode, -1 if no kernel takes it
+int shape_class(const HostShape& s, int jit_mode, int64_t n_bdds);
+// per-shape device descriptors and successor-code templates of out.shapes / out.shape_cls
+void build_templates(Decomposition& out);
 
 // BDD of { x in {0,1}^k : lo_bound <= sum a_t x_t <= hi_bound } (either bound optional).
 int build_row_shape(const std::vector<int64_t>& a, bool has_lo, int64_t lo_bound, bool has_hi, int64_t hi_bound,

@@ -65,6 +65,8 @@ struct fdog_instance {
 
     // decomposition and device state
     bool planned = false;
+    bool planned_on_device = false;  // the plan came from the device builder (plan_device.cu)
+    double plan_seconds = 0.0;       // wall time of building the decomposition
     bool built = false;
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -107,6 +109,13 @@ struct fdog_instance {
 
 namespace fdog {
 int plan(fdog_instance* inst, bool compile_jit = true);
+// device builder (plan_device.cu): FDOG_OK, plan_leave_to_host() when the
+// instance needs the host builder, or an FDOG_* error
+int plan_on_device(fdog_instance* inst, int jit_mode, bool fuse_local);
+int plan_leave_to_host();
+void free_device_plan(Decomposition& d, cudaStream_t s);
+// downloads the arrays of a device-built plan that host calls read
+int ensure_host_plan(fdog_instance* inst);
 size_t arena_size(const fdog_instance* inst);
 int fail_cuda(fdog_instance* inst, cudaError_t e, const char* where);
 cudaError_t copy_async(fdog_instance* inst, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);

@@ -52,6 +52,8 @@ int fdog_export_state(fdog_instance* inst, void* buf, size_t* bytes) {
     const size_t need = state_bytes(inst);
     if (!buf) { *bytes = need; return FDOG_OK; }
     if (*bytes < need) return FDOG_EINVAL;
+    int rc = ensure_host_plan(inst);  // the layout fingerprint reads the slot table
+    if (rc != FDOG_OK) return rc;
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != inst->device) cudaSetDevice(inst->device);
@@ -86,6 +88,8 @@ int fdog_import_state(fdog_instance* inst, const void* buf, size_t bytes) {
     if (!inst || !buf) return FDOG_EINVAL;
     if (!inst->built) return FDOG_ESTATE;
     if (bytes != state_bytes(inst)) return FDOG_EINVAL;
+    int rc = ensure_host_plan(inst);
+    if (rc != FDOG_OK) return rc;
     StateHeader h;
     std::memcpy(&h, buf, sizeof(h));
     if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1 || h.n_vars != inst->n_vars ||

@@ -627,53 +627,69 @@ int fdog_create(int32_t n_vars, const double* cost, int32_t n_rows, const int64_
         p.block_threads < 0 || p.block_threads > 1024 || (p.block_threads % 32) != 0 || p.grid_waves < -1 ||
         p.update < 0 || p.update > 1 || p.planner < 0 || p.planner > 2)
         return FDOG_EINVAL;
-    for (int32_t i = 0; i < n_vars; ++i)
-        if (!std::isfinite(cost[i])) return FDOG_EINVAL;
-    if (n_rows > 0) {
-        if (row_ptr[0] != 0) return FDOG_EINVAL;
-        for (int32_t j = 0; j < n_rows; ++j) {
-            if (row_ptr[j + 1] < row_ptr[j]) return FDOG_EINVAL;
-            if (sense[j] < -1 || sense[j] > 1) return FDOG_EINVAL;
-        }
-        const int64_t nnz = row_ptr[n_rows];
-        if (nnz > 0 && (!col || !coef)) return FDOG_EINVAL;
-        // columns in range and no column twice in a row, rows checked in parallel
-        std::atomic<bool> bad{false};
-        try {
-            parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
-                std::vector<int32_t> cols;
-                for (int64_t j = j0; j < j1 && !bad; ++j) {
-                    cols.assign(col + row_ptr[j], col + row_ptr[j + 1]);
-                    for (int32_t c : cols)
-                        if (c < 0 || c >= n_vars) { bad = true; break; }
-                    std::sort(cols.begin(), cols.end());
-                    if (std::adjacent_find(cols.begin(), cols.end()) != cols.end()) bad = true;
-                }
-            });
-        } catch (...) {
-            return FDOG_ENOMEM;
-        }
-        if (bad) return FDOG_EINVAL;
-    }
+    // copy and validate in one parallel pass per array (rows checked independently)
     fdog_instance* inst = new (std::nothrow) fdog_instance();
     if (!inst) return FDOG_ENOMEM;
     static std::atomic<uint64_t> next_uid{1};
     inst->uid = next_uid.fetch_add(1);
+    inst->n_vars = n_vars;
+    inst->n_rows = n_rows;
+    inst->params = p;
+    std::atomic<bool> bad{false};
+    int rc = FDOG_OK;
     try {
-        inst->n_vars = n_vars;
-        inst->n_rows = n_rows;
-        inst->params = p;
-        inst->cost.assign(cost, cost + n_vars);
-        inst->row_ptr.assign(row_ptr, row_ptr + (n_rows > 0 ? n_rows + 1 : 0));
-        if (inst->row_ptr.empty()) inst->row_ptr.push_back(0);
-        const int64_t nnz = inst->row_ptr.back();
-        inst->col.assign(col, col + nnz);
-        inst->coef.assign(coef, coef + nnz);
-        inst->sense.assign(sense, sense + n_rows);
-        inst->rhs.assign(rhs, rhs + n_rows);
+        inst->cost.resize(n_vars);
+        if (n_vars > 0) parallel_chunks(n_vars, [&](int64_t i0, int64_t i1) {
+            std::memcpy(inst->cost.data() + i0, cost + i0, sizeof(double) * (i1 - i0));
+            for (int64_t i = i0; i < i1; ++i)
+                if (!std::isfinite(cost[i])) { bad = true; break; }
+        });
+        inst->row_ptr.resize(n_rows + 1);
+        inst->row_ptr[0] = 0;
+        if (n_rows > 0 && row_ptr[0] != 0) bad = true;
+        inst->sense.resize(n_rows);
+        inst->rhs.resize(n_rows);
+        if (!bad && n_rows > 0) {
+            parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+                std::memcpy(inst->row_ptr.data() + j0 + 1, row_ptr + j0 + 1, sizeof(int64_t) * (j1 - j0));
+                std::memcpy(inst->sense.data() + j0, sense + j0, j1 - j0);
+                std::memcpy(inst->rhs.data() + j0, rhs + j0, sizeof(int64_t) * (j1 - j0));
+                for (int64_t j = j0; j < j1; ++j)
+                    if (row_ptr[j + 1] < row_ptr[j] || sense[j] < -1 || sense[j] > 1) { bad = true; break; }
+            });
+        }
+        const int64_t nnz = bad ? 0 : inst->row_ptr[n_rows];
+        if (!bad && nnz > 0 && (!col || !coef)) bad = true;
+        if (!bad && n_rows > 0) {
+            inst->col.resize(nnz);
+            inst->coef.resize(nnz);
+            // columns in range and no column twice in a row (rows in ascending
+            // column order pass without sorting)
+            parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+                const int64_t q0 = row_ptr[j0], q1 = row_ptr[j1];
+                std::memcpy(inst->col.data() + q0, col + q0, sizeof(int32_t) * (q1 - q0));
+                std::memcpy(inst->coef.data() + q0, coef + q0, sizeof(int32_t) * (q1 - q0));
+                std::vector<int32_t> cols;
+                for (int64_t j = j0; j < j1 && !bad; ++j) {
+                    bool ascending = true;
+                    for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q) {
+                        if (col[q] < 0 || col[q] >= n_vars) { bad = true; break; }
+                        if (q > row_ptr[j] && col[q] <= col[q - 1]) ascending = false;
+                    }
+                    if (ascending || bad) continue;
+                    cols.assign(col + row_ptr[j], col + row_ptr[j + 1]);
+                    std::sort(cols.begin(), cols.end());
+                    if (std::adjacent_find(cols.begin(), cols.end()) != cols.end()) bad = true;
+                }
+            });
+        }
     } catch (...) {
+        rc = FDOG_ENOMEM;
+    }
+    if (rc == FDOG_OK && bad) rc = FDOG_EINVAL;
+    if (rc != FDOG_OK) {
         delete inst;
-        return FDOG_ENOMEM;
+        return rc;
     }
     *out = inst;
     return FDOG_OK;

@@ -3,13 +3,39 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fdog_internal.h"
 #include "kernels.h"
 
 namespace fdog {
+
+// std::allocator whose value-less construct leaves trivial types
+// uninitialised: resize() then costs no fill pass over arrays that are
+// written right after (the instance's copy of the ILP).
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = DefaultInitAlloc<U>;
+    };
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+    }
+};
+template <class T>
+using HostArray = std::vector<T, DefaultInitAlloc<T>>;
 
 struct Engine;
 struct BatchView;
@@ -56,11 +82,11 @@ struct fdog_instance {
     // the ILP as given (copied at create)
     int32_t n_vars = 0;
     int32_t n_rows = 0;
-    std::vector<double> cost;
-    std::vector<int64_t> row_ptr;
-    std::vector<int32_t> col, coef;
-    std::vector<int8_t> sense;
-    std::vector<int64_t> rhs;
+    fdog::HostArray<double> cost;
+    fdog::HostArray<int64_t> row_ptr;
+    fdog::HostArray<int32_t> col, coef;
+    fdog::HostArray<int8_t> sense;
+    fdog::HostArray<int64_t> rhs;
     fdog_params params{};
 
     // decomposition and device state

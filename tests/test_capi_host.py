@@ -47,6 +47,7 @@ def test_params_defaults(P):
     p = P.capi.default_params()
     assert (p.omega, p.delta, p.alpha, p.tol) == (0.5, 1.0, 1.2, 1e-4)
     assert (p.window, p.min_iters, p.rounding_dual_iters, p.max_rounds) == (10, 20, 20, 200)
+    assert (p.update, p.planner) == (0, 0)
 
 
 def test_create_rejects_malformed_input(P):
@@ -68,7 +69,16 @@ def test_create_rejects_malformed_input(P):
         with pytest.raises(P.FdogError) as e:
             P.Instance(**args)
         assert e.value.code == P.FDOG_EINVAL
-    for kw in (dict(omega=0.0), dict(omega=1.5), dict(window=0), dict(block_threads=48)):
+    # a row listed out of column order is valid; a repeat anywhere in it is not
+    b0, b1 = int(g.row_ptr[0]), int(g.row_ptr[1])
+    assert b1 - b0 >= 3
+    perm = g.col.copy(); perm[b0:b1] = perm[b0:b1][::-1]
+    P.Instance(n_vars=g.n_vars, cost=g.cost, row_ptr=g.row_ptr, col=perm, coef=g.coef, sense=g.sense, rhs=g.rhs)
+    rep = perm.copy(); rep[b1 - 1] = rep[b0]
+    with pytest.raises(P.FdogError) as e:
+        P.Instance(n_vars=g.n_vars, cost=g.cost, row_ptr=g.row_ptr, col=rep, coef=g.coef, sense=g.sense, rhs=g.rhs)
+    assert e.value.code == P.FDOG_EINVAL
+    for kw in (dict(omega=0.0), dict(omega=1.5), dict(window=0), dict(block_threads=48), dict(planner=3)):
         with pytest.raises(P.FdogError) as e:
             P.Instance.from_ilp(g, **kw)
         assert e.value.code == P.FDOG_EINVAL

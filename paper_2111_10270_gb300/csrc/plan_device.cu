@@ -102,24 +102,38 @@ __global__ void row_signature_kernel(const int64_t* __restrict__ row_ptr, const 
 }
 
 // Items with key 0 take no slot.  tval keeps the smallest item of each key.
+// Lanes of a warp with equal keys insert once (their lowest lane, which holds
+// the smallest item), and a slot is read before it is touched atomically, so
+// that millions of rows sharing a handful of signatures do not serialise on
+// one address.
 __global__ void key_insert_kernel(const uint64_t* __restrict__ key, int32_t n, unsigned long long* tkey,
                                   int32_t* tval, int32_t* __restrict__ slot_of, uint32_t mask, PlanFlags* f) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const unsigned long long k = key[i];
-    if (k == 0) { slot_of[i] = -1; return; }
-    uint32_t s = static_cast<uint32_t>(k >> 20) & mask;
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long prev = atomicCAS(&tkey[s], 0ull, k);
-        if (prev == 0ull || prev == k) {
-            atomicMin(&tval[s], i);
-            slot_of[i] = static_cast<int32_t>(s);
-            return;
+    const int lane = threadIdx.x & 31;
+    const unsigned long long k = i < n ? key[i] : 0ull;
+    const unsigned peers = __match_any_sync(kFull, k);
+    const int leader = __ffs(peers) - 1;
+    int32_t slot = -1;
+    if (k != 0ull && lane == leader) {
+        uint32_t s = static_cast<uint32_t>(k >> 20) & mask;
+        for (uint32_t probe = 0; probe <= mask; ++probe) {
+            unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&tkey[s]);
+            if (cur == 0ull) {
+                cur = atomicCAS(&tkey[s], 0ull, k);
+                if (cur == 0ull) cur = k;
+            }
+            if (cur == k) {
+                // values only decrease, so a stale read is never below the current minimum
+                if (i < *reinterpret_cast<volatile int32_t*>(&tval[s])) atomicMin(&tval[s], i);
+                slot = static_cast<int32_t>(s);
+                break;
+            }
+            s = (s + 1) & mask;
         }
-        s = (s + 1) & mask;
+        if (slot < 0) atomicOr(&f->host, kHostTable);
     }
-    slot_of[i] = -1;
-    atomicOr(&f->host, kHostTable);
+    slot = __shfl_sync(kFull, slot, leader);
+    if (i < n) slot_of[i] = k != 0ull ? slot : -1;
 }
 
 __global__ void row_verify_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ coef,
@@ -289,9 +303,8 @@ __global__ void slot_count_kernel(const int32_t* __restrict__ var, int64_t S, in
 
 __global__ void outside_count_kernel(const int32_t* __restrict__ cnt, int32_t n, PlanFlags* f) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool zero = i < n && cnt[i] == 0;
-    const unsigned bal = __ballot_sync(kFull, zero);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&f->n_outside, __popc(bal));
+    const int zeros = __syncthreads_count(i < n && cnt[i] == 0);
+    if (threadIdx.x == 0 && zeros) atomicAdd(&f->n_outside, zeros);
 }
 
 __global__ void slot_scatter_kernel(const int32_t* __restrict__ var, int64_t S, const int32_t* __restrict__ off,
@@ -318,18 +331,22 @@ __global__ void slot_rank_kernel(const int32_t* __restrict__ var, int64_t S, con
 // ---- 6: tile-local variables -----------------------------------------------
 // A variable is tile-local when all of its (at most four) copies lie in one
 // tile of a row of at most kEpiMaxK layers; it is listed at its first copy.
+// FILL: writes the entries and the tile's key, a sum over its entries of
+// mix64(index, value) (order-dependent through the index; equal keys are
+// verified entry by entry afterwards), 0 for a tile without entries.
 template <bool FILL>
 __global__ void tile_local_kernel(const TileDev* __restrict__ tiles, const int32_t* __restrict__ shape_k,
                                   int32_t nt, const int32_t* __restrict__ var, const int32_t* __restrict__ off,
                                   const int32_t* __restrict__ pos, int32_t* __restrict__ ent_cnt,
                                   const int32_t* __restrict__ ent_off, uint16_t* __restrict__ ents,
-                                  uint8_t* __restrict__ local) {
+                                  uint8_t* __restrict__ local, uint64_t* __restrict__ key) {
     const int32_t ti = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (ti >= nt) return;
     const TileDev t = tiles[ti];
     const int k = shape_k[t.shape];
     int32_t m = 0;
+    uint64_t h = 0;
     if (k <= kEpiMaxK) {
         const int64_t lo = t.slot_base, hi = lo + static_cast<int64_t>(k) * kTile;
         for (int layer = 0; layer < k; ++layer) {
@@ -344,43 +361,47 @@ __global__ void tile_local_kernel(const TileDev* __restrict__ tiles, const int32
             }
             const unsigned bal = __ballot_sync(kFull, hit);
             if (FILL && hit) {
-                uint16_t* dst = ents + ent_off[ti] + 4 * (m + __popc(bal & lanemask_lt()));
+                const int32_t idx = 4 * (m + __popc(bal & lanemask_lt()));
+                uint16_t* dst = ents + ent_off[ti] + idx;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dst[q] = q < c ? static_cast<uint16_t>(pos[b + q] - lo) : uint16_t(0xFFFF);
+                for (int q = 0; q < 4; ++q) {
+                    const uint16_t e = q < c ? static_cast<uint16_t>(pos[b + q] - lo) : uint16_t(0xFFFF);
+                    dst[q] = e;
+                    h += mix64((static_cast<uint64_t>(idx + q) << 16) | e);
+                }
                 local[v] = 1;
             }
             m += __popc(bal);
         }
     }
     if (!FILL && lane == 0) ent_cnt[ti] = 4 * m;
+    if (FILL) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) h += __shfl_xor_sync(kFull, h, d);
+        if (lane == 0) {
+            h = m ? mix64(h ^ static_cast<uint64_t>(m)) : 0ull;
+            key[ti] = m && h == 0ull ? 1ull : h;
+        }
+    }
 }
 
-__global__ void tile_key_kernel(const int32_t* __restrict__ ent_off, int32_t nt, const uint16_t* __restrict__ ents,
-                                uint64_t* __restrict__ key) {
-    const int32_t ti = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ti >= nt) return;
-    const int32_t b = ent_off[ti], e = ent_off[ti + 1];
-    if (b == e) { key[ti] = 0; return; }
-    uint64_t h = mix64(static_cast<uint64_t>(e - b));
-    for (int32_t q = b; q < e; ++q) h = mix64(h ^ ents[q]);
-    key[ti] = h ? h : 1;
-}
-
+// a warp per tile: representative tiles are listed, the others compared with theirs
 __global__ void tile_verify_kernel(const int32_t* __restrict__ ent_off, int32_t nt, const uint16_t* __restrict__ ents,
                                    const int32_t* __restrict__ slot_of, const int32_t* __restrict__ tval,
                                    int32_t* reps, PlanFlags* f) {
-    const int32_t ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t ti = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (ti >= nt) return;
     const int32_t s = slot_of[ti];
     if (s < 0) return;
     const int32_t r = tval[s];
     if (r == ti) {
-        reps[atomicAdd(&f->n_reps, 1)] = ti;  // at most nt representatives
+        if (lane == 0) reps[atomicAdd(&f->n_reps, 1)] = ti;  // at most nt representatives
         return;
     }
     const int32_t len = ent_off[ti + 1] - ent_off[ti];
     bool same = len == ent_off[r + 1] - ent_off[r];
-    for (int32_t q = 0; same && q < len; ++q) same = ents[ent_off[ti] + q] == ents[ent_off[r] + q];
+    for (int32_t q = lane; same && q < len; q += 32) same = ents[ent_off[ti] + q] == ents[ent_off[r] + q];
     if (!same) atomicOr(&f->host, kHostCollision);
 }
 
@@ -413,8 +434,8 @@ __global__ void var_bucket_kernel(const int32_t* __restrict__ off, int32_t n, co
         if (!loc && c > 0) k = min(c, FDOG_WBUCKETS) - 1;
         key[i] = k;
     }
-    const unsigned bal = __ballot_sync(kFull, loc);
-    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(&f->n_local, static_cast<unsigned long long>(__popc(bal)));
+    const int n_loc = __syncthreads_count(loc);
+    if (threadIdx.x == 0 && n_loc) atomicAdd(&f->n_local, static_cast<unsigned long long>(n_loc));
     if (k == FDOG_WBUCKETS - 1) atomicAdd(&f->overflow_slots, static_cast<unsigned long long>(c));
 }
 
@@ -713,7 +734,7 @@ int plan_on_device(fdog_instance* inst, int jit_mode, bool fuse_local) {
         PLAN_CHECK(cudaMemsetAsync(d_ent_off, 0, sizeof(int32_t) * (static_cast<size_t>(nt) + 1), st));
         const unsigned tgrid = grid_of(static_cast<int64_t>(nt) * 32, 256);
         tile_local_kernel<false><<<tgrid, 256, 0, st>>>(d_tiles, d_shape_k, nt, out.d_var, out.d_csr_off,
-                                                        out.d_csr_pos, d_ent_off, nullptr, nullptr, nullptr);
+                                                        out.d_csr_pos, d_ent_off, nullptr, nullptr, nullptr, nullptr);
         PLAN_CHECK(cudaGetLastError());
         PLAN_CHECK(device_scan(d_ent_off, static_cast<int64_t>(nt) + 1, sc));
         std::vector<int32_t> ent_off(static_cast<size_t>(nt) + 1);
@@ -732,13 +753,13 @@ int plan_on_device(fdog_instance* inst, int jit_mode, bool fuse_local) {
             int32_t* d_tpat = sc.get<int32_t>(nt);
             if (sc.err != cudaSuccess) return fail(sc.err);
             tile_local_kernel<true><<<tgrid, 256, 0, st>>>(d_tiles, d_shape_k, nt, out.d_var, out.d_csr_off,
-                                                           out.d_csr_pos, nullptr, d_ent_off, d_ents, d_local);
+                                                           out.d_csr_pos, nullptr, d_ent_off, d_ents, d_local,
+                                                           d_tkey2);
             PLAN_CHECK(cudaMemsetAsync(d_ttab, 0, sizeof(unsigned long long) * (static_cast<size_t>(tmask) + 1), st));
             PLAN_CHECK(cudaMemsetAsync(d_tval2, 0x7F, sizeof(int32_t) * (static_cast<size_t>(tmask) + 1), st));
             PLAN_CHECK(cudaMemsetAsync(&d_f->n_reps, 0, sizeof(int32_t), st));
-            tile_key_kernel<<<grid_of(nt, 256), 256, 0, st>>>(d_ent_off, nt, d_ents, d_tkey2);
             key_insert_kernel<<<grid_of(nt, 256), 256, 0, st>>>(d_tkey2, nt, d_ttab, d_tval2, d_tslot, tmask, d_f);
-            tile_verify_kernel<<<grid_of(nt, 256), 256, 0, st>>>(d_ent_off, nt, d_ents, d_tslot, d_tval2, d_treps, d_f);
+            tile_verify_kernel<<<tgrid, 256, 0, st>>>(d_ent_off, nt, d_ents, d_tslot, d_tval2, d_treps, d_f);
             PLAN_CHECK(cudaGetLastError());
             PLAN_CHECK(read_flags());
             if (hf.host) return leave();

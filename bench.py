@@ -50,7 +50,8 @@ WORKLOADS = {
 }
 METRIC = "BDD arc-updates/s (full FastDOG solve: dual sweeps to the 1e-4 LB gap + perturbation rounding)"
 UNIT = "arc-updates/s"
-SWEEP_SRCS = [os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", f) for f in ("jit.cpp", "jit_skeleton.cuh")]
+SWEEP_SRCS = [os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", f)
+              for f in ("jit.cpp", "jit_skeleton.cuh", "kernels.cu")]  # generator, skeleton, launch (L2 window)
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_traffic.txt")
 
 

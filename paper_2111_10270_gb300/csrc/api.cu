@@ -308,6 +308,7 @@ int allocate_and_upload(fdog_instance* inst) {
     b.insts = a.inst;
     b.n_inst = 1;
     b.jit = inst->jit;
+    b.l2 = l2_window_for(inst->device, a.T, sizeof(float) * n);
     int q = 0;
     for (int c = 0; c < kNumClasses; ++c) {
         pre[q] = 0;

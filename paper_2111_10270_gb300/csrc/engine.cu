@@ -84,6 +84,7 @@ int view_build(Engine& e, BatchView& v, const std::vector<fdog_instance*>& membe
             if (s.jit >= 0) ids.push_back(s.jit);
     }
     b.insts = reinterpret_cast<InstDev*>(dbase);
+    if (n == 1) b.l2 = members[0]->batch.l2;  // the instance's deferred terms stay in L2 during its sweeps
     for (int c = 0; c < kNumClasses; ++c) {
         int32_t* pre = ints + q;
         int32_t* first = ints + q + n + 1;

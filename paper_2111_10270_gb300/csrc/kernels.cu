@@ -514,6 +514,8 @@ cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, con
     const bool timed = cfg.prof && cfg.prof->on && (mode == kFwdUpdate || mode == kBwdUpdate);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+    // update passes of the dominant class keep the deferred terms they gather in L2
+    const L2Window l2 = dominant && (mode == kFwdUpdate || mode == kBwdUpdate) ? b.l2 : L2Window();
     cudaError_t e;
     if (cls == kJitClass) {
         void* kargs[] = {&args};
@@ -521,12 +523,12 @@ cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, con
         if (smem > 48 * 1024)
             e = cudaFuncSetAttribute(b.jit.fn[mode], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem));
-        if (e == cudaSuccess) e = cudaLaunchKernel(b.jit.fn[mode], dim3(blocks), dim3(32 * wpb), kargs, smem, s);
+        if (e == cudaSuccess) e = launch_windowed(b.jit.fn[mode], blocks, 32 * wpb, kargs, smem, s, l2);
     } else switch (W) {
-        case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-        case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-        case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
-        default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args); break;
+        case 2: e = launch_sweep_width<2>(reg, mode, blocks, 32 * wpb, smem, s, args, l2); break;
+        case 4: e = launch_sweep_width<4>(reg, mode, blocks, 32 * wpb, smem, s, args, l2); break;
+        case 8: e = launch_sweep_width<8>(reg, mode, blocks, 32 * wpb, smem, s, args, l2); break;
+        default: e = launch_sweep_width<16>(reg, mode, blocks, 32 * wpb, smem, s, args, l2); break;
     }
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(dominant ? 0 : 2, ev0, ev1); }
     cfg.count();
@@ -537,6 +539,47 @@ cudaError_t launch_class(const DevBatch& b, int cls, int mode, int mm_flags, con
 bool can_fork(const LaunchCfg& cfg) { return cfg.side && cfg.side->ready; }
 
 }  // namespace
+
+cudaError_t launch_windowed(const void* fn, int blocks, int threads, void** args, size_t smem, cudaStream_t s,
+                            const L2Window& l2) {
+    if (l2.bytes == 0) return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, s);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow.base_ptr = l2.base;
+    attr[0].val.accessPolicyWindow.num_bytes = l2.bytes;
+    attr[0].val.accessPolicyWindow.hitRatio = l2.hit_ratio;
+    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchConfig_t c{};
+    c.gridDim = dim3(blocks);
+    c.blockDim = dim3(threads);
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    c.attrs = attr;
+    c.numAttrs = 1;
+    return cudaLaunchKernelExC(&c, fn, args);
+}
+
+L2Window l2_window_for(int device, void* base, size_t bytes) {
+    L2Window w;
+    int pmax = 0, wmax = 0;
+    if (bytes == 0 || cudaDeviceGetAttribute(&pmax, cudaDevAttrMaxPersistingL2CacheSize, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&wmax, cudaDevAttrMaxAccessPolicyWindowSize, device) != cudaSuccess || pmax <= 0 ||
+        wmax <= 0) {
+        cudaGetLastError();
+        return w;
+    }
+    const size_t want = std::min<size_t>(bytes, static_cast<size_t>(pmax));
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) cur = 0;
+    if (cur < want && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) == cudaSuccess) cur = want;
+    cudaGetLastError();
+    if (cur == 0) return w;
+    w.base = base;
+    w.bytes = std::min<size_t>(bytes, static_cast<size_t>(wmax));
+    w.hit_ratio = std::min(1.0f, static_cast<float>(cur) / static_cast<float>(w.bytes));
+    return w;
+}
 
 int SideStreams::create(int device) {
     if (ready) return cudaSuccess;

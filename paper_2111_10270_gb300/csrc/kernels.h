@@ -41,6 +41,20 @@ struct SerialPlan {
     const int32_t* lev_b = nullptr;
 };
 
+// L2 access-policy window of a launch: lines of [base, base + bytes) are
+// kept in the device's persisting L2 carve-out (0 bytes: no window).  Used
+// for one instance's deferred terms T, which every update sweep gathers at
+// scattered positions.
+struct L2Window {
+    void* base = nullptr;
+    size_t bytes = 0;
+    float hit_ratio = 0.f;
+};
+
+// Raises the device's persisting-L2 carve-out to hold `bytes` (capped by the
+// device maximum; never lowered) and returns the window for [base, base + bytes).
+L2Window l2_window_for(int device, void* base, size_t bytes);
+
 struct FlatArgsS {
     const InstDev* I;
     int32_t total;
@@ -70,6 +84,7 @@ struct DevBatch {
     int32_t n_inst = 0;
     JitKernels jit;                          // kernels of the shape-specialised class
     SerialPlan serial;                       // serial update only
+    L2Window l2;                             // update sweeps of a one-instance batch: its T array
 };
 
 

@@ -688,15 +688,19 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
 
 }  // namespace dev
 
+// a kernel launch with an optional L2 access-policy window (kernels.cu)
+cudaError_t launch_windowed(const void* fn, int blocks, int threads, void** args, size_t smem, cudaStream_t s,
+                            const L2Window& l2);
+
 // host-side dispatch of one width's instantiations (defined in sweep_w<W>.cu)
 template <int W>
 cudaError_t launch_sweep_width(bool reg, int mode, int blocks, int threads, size_t smem, cudaStream_t s,
-                               const SweepArgs& a);
+                               const SweepArgs& a, const L2Window& l2);
 
 #define FDOG_DEFINE_SWEEP_WIDTH(W, HAS_REG)                                                                    \
     template <>                                                                                                \
     cudaError_t launch_sweep_width<W>(bool reg, int mode, int blocks, int threads, size_t smem, cudaStream_t s, \
-                                      const SweepArgs& a) {                                                    \
+                                      const SweepArgs& a, const L2Window& l2) {                                \
         void (*fn)(SweepArgs) = nullptr;                                                                       \
         if (HAS_REG && reg) {                                                                                  \
             fn = mode == kFwdUpdate ? dev::sweep_kernel<W, HAS_REG, kFwdUpdate>                                \
@@ -719,8 +723,8 @@ cudaError_t launch_sweep_width(bool reg, int mode, int blocks, int threads, size
                                                  static_cast<int>(smem));                                      \
             if (e != cudaSuccess) return e;                                                                    \
         }                                                                                                      \
-        fn<<<blocks, threads, smem, s>>>(a);                                                                   \
-        return cudaGetLastError();                                                                             \
+        void* args[] = {const_cast<SweepArgs*>(&a)};                                                           \
+        return launch_windowed(reinterpret_cast<const void*>(fn), blocks, threads, args, smem, s, l2);         \
     }
 
 }  // namespace fdog

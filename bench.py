@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--serve-instances", type=int, default=48,
                     help="requests of the serving stream replayed in the serving section (0: skip)")
     ap.add_argument("--schemes", type=int, default=1, help="update-scheme comparison section (0: skip)")
+    ap.add_argument("--split", type=int, default=1, help="long-row splitting section (0: skip)")
     ap.add_argument("--threads", type=int, default=min(16, os.cpu_count() or 1),
                     help="host threads / processes for instance generation and planning")
     return ap.parse_args()
@@ -452,6 +453,47 @@ def update_scheme_section(P, dev, stream):
     return out
 
 
+def split_section(torch, P, dev, stream):
+    """The 500x1000 QAP-shaped matching with its long at-most-one rows as
+    given and split into chains of at most 8 or 5 variables
+    (fdog_split_rows): dual iterations to the 1e-4 stopping rule and the bound
+    there, the bound after 1500 iterations without early stop, the device
+    time per iteration, and how many tiles the segmented (long-row) kernels
+    still run."""
+    import ilpgen
+
+    g = ilpgen.qap(2, 500, 1000, 20, 10)
+    cases = {}
+    for max_len in (None, 8, 5):
+        if max_len is None:
+            s, key = g, "as given"
+        else:
+            nv, rp, col, coef, sense, rhs, _ = P.capi.split_rows(g.n_vars, g.row_ptr, g.col, g.coef, g.sense,
+                                                                 g.rhs, max_len)
+            s = ilpgen.ILP(nv, np.concatenate([g.cost, np.zeros(nv - g.n_vars)]), rp, col, coef, sense, rhs)
+            key = f"split, rows of at most {max_len}"
+        inst = P.Instance.from_ilp(s, tol=1e-4).build(dev, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_stop, lb_stop = inst.iterate(3000)
+        torch.cuda.synchronize()
+        t_stop = time.perf_counter() - t0
+        seg_tiles = inst.kernel_plan()["static_tiles"]
+        inst.close()
+        inst = P.Instance.from_ilp(s, tol=0.0).build(dev, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, lb_fixed = inst.iterate(1500)
+        torch.cuda.synchronize()
+        ms_iter = (time.perf_counter() - t0) / 1500 * 1e3
+        inst.close()
+        cases[key] = {"vars": int(s.n_vars), "rows": int(len(s.row_ptr) - 1),
+                      "max_row": int(np.diff(s.row_ptr).max()), "iters_to_stop": int(n_stop),
+                      "bound_at_stop": float(lb_stop), "seconds_to_stop": t_stop, "bound_after_1500": float(lb_fixed),
+                      "ms_per_iter": ms_iter, "generic_kernel_tiles": int(seg_tiles)}
+    return {"instance": "QAP-shaped matching 500x1000, 20 candidates, 10-NN AND products, seed 2", "cases": cases}
+
+
 def sweep_traffic(workload):
     """DRAM bytes per update-sweep launch from the committed ncu summary (of
     the 512x512 MRF), if the sweep's generator sources are unchanged since."""
@@ -605,9 +647,11 @@ def main():
                          f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
 
     # ---- batched and served instance mixes (rank 0, N = 1) ---------------------
-    batched = served = schemes = None
+    batched = served = schemes = split = None
     if rank == 0 and world == 1 and args.schemes:
         schemes = update_scheme_section(P, dev, stream)
+    if rank == 0 and world == 1 and args.split:
+        split = split_section(torch, P, dev, stream)
     if rank == 0 and world == 1 and args.batch_instances > 0:
         batched = batched_section(torch, P, dev, stream, params, args.batch_instances, args.threads)
     if rank == 0 and world == 1 and args.serve_instances > 0:
@@ -626,7 +670,7 @@ def main():
                               else f"inputs fit in L2 ({dev_bytes / 1e6:.0f} MB resident); no flush between steps"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "batched": batched, "serving": served, "update_schemes": schemes,
+            "batched": batched, "serving": served, "update_schemes": schemes, "long_rows": split,
         }
         print(json.dumps(line), flush=True)
     inst.close()

@@ -208,6 +208,33 @@ int fdog_plan_stats(fdog_instance* inst, int32_t* on_device, double* seconds);
 int fdog_plan_digest(fdog_instance* inst, uint64_t* digest);
 
 /*
+ * Long-row splitting (the paper's conclusion names long rows as future
+ * work): a transformation of an ILP given in the fdog_create form, applied by
+ * the caller before fdog_create.  Every row sum_{i in I} x_i <= 1 or = 1
+ * (all coefficients 1, right-hand side 1) with |I| > max_len becomes a chain
+ * of rows of at most max_len variables joined by new binary variables
+ * y_1 .. y_{m-1} (numbered from n_vars on, cost 0 for the caller to append):
+ *   sum_{P_1} x - y_1 = 0,  sum_{P_j} x + y_{j-1} - y_j = 0,
+ *   sum_{P_m} x + y_{m-1} <= 1 (= 1),
+ * with |P_1| = max_len - 1, |P_j| = max_len - 2 and |P_m| <= max_len - 1, the
+ * entries of P in the row's order.  Pieces share one binary variable each, so
+ * the split rows have the same convex hull over x as the original row and the
+ * decomposition the same optimal bound, with BDDs of at most max_len layers.
+ * Other rows are copied unchanged; pieces replace their row in place, and
+ * out_row_origin (may be NULL) gives each new row's original row.
+ * Size query: out_row_ptr NULL writes *out_n_vars, *out_n_rows, *out_nnz;
+ * otherwise those give the capacities of the caller's arrays
+ * (out_row_ptr[*out_n_rows + 1], out_col / out_coef[*out_nnz],
+ * out_sense / out_rhs / out_row_origin[*out_n_rows]) and receive the sizes.
+ * Errors: FDOG_EINVAL (max_len < 3, malformed CSR, NULL pointers, capacity
+ * too small), FDOG_EUNSUPPORTED (more than 2^31 - 1 variables or rows).
+ */
+int fdog_split_rows(int32_t n_vars, int32_t n_rows, const int64_t* row_ptr, const int32_t* col, const int32_t* coef,
+                    const int8_t* sense, const int64_t* rhs, int32_t max_len, int32_t* out_n_vars,
+                    int32_t* out_n_rows, int64_t* out_nnz, int64_t* out_row_ptr, int32_t* out_col,
+                    int32_t* out_coef, int8_t* out_sense, int64_t* out_rhs, int32_t* out_row_origin);
+
+/*
  * Build the decomposition and upload it to `device` on `cuda_stream`:
  * presolve (fix variables a row forces, drop rows every assignment
  * satisfies), one reduced ordered BDD per remaining row over its variables in

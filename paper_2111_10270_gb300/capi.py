@@ -66,6 +66,8 @@ SIGNATURES = {
     "fdog_fixed_vars": (ctypes.c_int, [_P, _P]),
     "fdog_plan_stats": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
     "fdog_plan_digest": (ctypes.c_int, [_P, _P]),
+    "fdog_split_rows": (ctypes.c_int, [_i32, _i32, _P, _P, _P, _P, _P, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                       ctypes.POINTER(_i64), _P, _P, _P, _P, _P, _P]),
     "fdog_kernel_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                         ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                         ctypes.c_char_p, _i32]),
@@ -137,6 +139,37 @@ class FdogError(RuntimeError):
 
 def _ptr(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def split_rows(n_vars, row_ptr, col, coef, sense, rhs, max_len: int):
+    """fdog_split_rows: long at-most-one / exactly-one rows as chains of rows
+    of at most max_len variables joined by new binaries (numbered from
+    n_vars).  Returns (n_vars, row_ptr, col, coef, sense, rhs, row_origin)."""
+    L = lib()
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    coef = np.ascontiguousarray(coef, np.int32)
+    sense = np.ascontiguousarray(sense, np.int8)
+    rhs = np.ascontiguousarray(rhs, np.int64)
+    n_rows = len(row_ptr) - 1
+    nv, nr, nnz = _i32(), _i32(), _i64()
+    args = (int(n_vars), n_rows, _ptr(row_ptr), _ptr(col), _ptr(coef), _ptr(sense), _ptr(rhs), int(max_len))
+    rc = L.fdog_split_rows(*args, ctypes.byref(nv), ctypes.byref(nr), ctypes.byref(nnz), None, None, None, None,
+                           None, None)
+    if rc != FDOG_OK:
+        raise FdogError(rc, "fdog_split_rows")
+    o_ptr = np.zeros(nr.value + 1, np.int64)
+    o_col = np.zeros(max(nnz.value, 1), np.int32)
+    o_coef = np.zeros(max(nnz.value, 1), np.int32)
+    o_sense = np.zeros(max(nr.value, 1), np.int8)
+    o_rhs = np.zeros(max(nr.value, 1), np.int64)
+    o_orig = np.zeros(max(nr.value, 1), np.int32)
+    rc = L.fdog_split_rows(*args, ctypes.byref(nv), ctypes.byref(nr), ctypes.byref(nnz), _ptr(o_ptr), _ptr(o_col),
+                           _ptr(o_coef), _ptr(o_sense), _ptr(o_rhs), _ptr(o_orig))
+    if rc != FDOG_OK:
+        raise FdogError(rc, "fdog_split_rows")
+    m, k = nr.value, nnz.value
+    return nv.value, o_ptr, o_col[:k], o_coef[:k], o_sense[:m], o_rhs[:m], o_orig[:m]
 
 
 def default_params(**kw) -> Params:

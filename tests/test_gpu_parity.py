@@ -285,6 +285,33 @@ def long_narrow_rows(seed=6):
     return rb.finish(n, rng.standard_normal(n), "long-narrow")
 
 
+def split_ilp(P, g, max_len):
+    nv, rp, col, coef, sense, rhs, _ = P.capi.split_rows(g.n_vars, g.row_ptr, g.col, g.coef, g.sense, g.rhs,
+                                                         max_len)
+    return ilpgen.ILP(nv, np.concatenate([g.cost, np.zeros(nv - g.n_vars)]), rp, col, coef, sense, rhs,
+                      name=g.name + "-split")
+
+
+@pytest.mark.parametrize("kind", ["qap", "long"])
+def test_split_rows_parity(P, oracle_mod, kind):
+    """An ILP whose long at-most-one / exactly-one rows were split into chains
+    (fdog_split_rows) is an ILP like any other: bound trajectory and
+    min-marginals against the oracle on the split ILP; the split rows run in
+    the register kernels (no segmented class left for them)."""
+    g = ilpgen.qap(11, 14, 28, 6, 3) if kind == "qap" else long_narrow_rows()
+    s = split_ilp(P, g, 6)
+    assert s.n_vars > g.n_vars
+    inst, orc, gl, ol, cond = trajectory(P, oracle_mod, s, 40)
+    bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
+    assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    if kind == "qap":
+        assert np.diff(s.row_ptr).max() <= 6
+
+
 @pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
 def test_long_narrow_rows_parity(P, oracle_mod, jit):
     """The segmented kernels (registers per segment of 8 layers, labels

@@ -299,7 +299,8 @@ def test_split_rows_parity(P, oracle_mod, kind):
     min-marginals against the oracle on the split ILP; the split rows run in
     the register kernels (no segmented class left for them)."""
     g = ilpgen.qap(11, 14, 28, 6, 3) if kind == "qap" else long_narrow_rows()
-    s = split_ilp(P, g, 6)
+    max_len = 4 if kind == "qap" else 6
+    s = split_ilp(P, g, max_len)
     assert s.n_vars > g.n_vars
     inst, orc, gl, ol, cond = trajectory(P, oracle_mod, s, 40)
     bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
@@ -309,7 +310,7 @@ def test_split_rows_parity(P, oracle_mod, kind):
     perm = slot_order(orc, var, row)
     assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
     if kind == "qap":
-        assert np.diff(s.row_ptr).max() <= 6
+        assert np.diff(s.row_ptr).max() <= max_len
 
 
 @pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])

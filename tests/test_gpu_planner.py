@@ -142,3 +142,50 @@ def test_full_size_mrf_device_plan_equals_host_plan(P):
     on_dev, sec = d.plan_stats()
     assert on_dev and sec > 0
     assert np.array_equal(h.plan_digest(), d.plan_digest())
+
+
+def rows_ilp(n, rows, seed):
+    """ILP from (cols, coefs, sense, rhs) rows with normal costs."""
+    rng = np.random.default_rng(seed)
+    row_ptr = np.cumsum([0] + [len(r[0]) for r in rows]).astype(np.int64)
+    return ilpgen.ILP(n, rng.normal(size=n), row_ptr, np.concatenate([r[0] for r in rows]).astype(np.int32),
+                      np.concatenate([r[1] for r in rows]).astype(np.int32),
+                      np.array([r[2] for r in rows], np.int8), np.array([r[3] for r in rows], np.int64))
+
+
+def many_signatures():
+    """1,080 distinct row signatures (sum x <= b for every length k in 2..80
+    and b in 1..min(15, k - 1)): more than the device builder takes."""
+    rng = np.random.default_rng(7)
+    rows = [(np.sort(rng.choice(3000, k, replace=False)), np.ones(k, int), -1, b)
+            for k in range(2, 81) for b in range(1, min(15, k - 1) + 1)]
+    return rows_ilp(3000, rows, 7)
+
+
+def hub_variable():
+    """x_0 + x_j <= 1 for j = 1..5000: x_0 has 5,000 copies."""
+    return rows_ilp(5001, [(np.array([0, j]), np.ones(2, int), -1, 1) for j in range(1, 5001)], 8)
+
+
+def unsorted_rows():
+    """A small MRF with every row listed in descending column order."""
+    g = ilpgen.mrf_grid(6, 6, 3, seed=9)
+    col, coef = g.col.copy(), g.coef.copy()
+    for j in range(len(g.row_ptr) - 1):
+        b, e = g.row_ptr[j], g.row_ptr[j + 1]
+        col[b:e], coef[b:e] = col[b:e][::-1], coef[b:e][::-1]
+    return dataclasses.replace(g, col=col, coef=coef)
+
+
+@pytest.mark.parametrize("make", [many_signatures, hub_variable, unsorted_rows],
+                         ids=["signatures", "copies", "unsorted"])
+def test_instances_beyond_the_device_builder_fall_back(P, make):
+    ilp = make()
+    h = built(P, ilp, 1)
+    d = built(P, ilp, 0)
+    assert not d.plan_stats()[0]
+    assert np.array_equal(h.plan_digest(), d.plan_digest())
+    assert h.iterate(5) == d.iterate(5)
+    with pytest.raises(P.FdogError) as err:
+        built(P, ilp, 2)
+    assert err.value.code == P.capi.FDOG_EUNSUPPORTED

@@ -217,3 +217,31 @@ def test_build_without_gpu_fails_loudly(P):
     inst = P.Instance.from_ilp(ilpgen.fig2_example())
     with pytest.raises(P.FdogError):
         inst.build(0)
+
+
+def test_plan_digest_and_stats_on_host_plans(P):
+    g = ilpgen.mrf_grid(6, 5, 3, seed=4)
+    a = P.Instance.from_ilp(g)
+    a.plan()
+    b = P.Instance.from_ilp(g)
+    b.plan()
+    on_dev, sec = a.plan_stats()
+    assert not on_dev and sec > 0
+    da, db = a.plan_digest(), b.plan_digest()
+    assert len(da) == P.capi.PLAN_DIGESTS and np.array_equal(da, db)
+    # one right-hand side changed: the presolve constants and layout stay, the shapes do not
+    rhs = g.rhs.copy()
+    j = int(np.argmax(np.diff(g.row_ptr)))
+    rhs[j] += 1
+    c = P.Instance(n_vars=g.n_vars, cost=g.cost, row_ptr=g.row_ptr, col=g.col, coef=g.coef, sense=g.sense, rhs=rhs)
+    c.plan()
+    dc = c.plan_digest()
+    assert dc[1] != da[1]
+    # costs only enter the presolve constants (none here: every variable is in a row)
+    d = P.Instance(n_vars=g.n_vars, cost=g.cost + 1.0, row_ptr=g.row_ptr, col=g.col, coef=g.coef, sense=g.sense,
+                   rhs=g.rhs)
+    d.plan()
+    assert np.array_equal(d.plan_digest(), da)
+    with pytest.raises(P.FdogError) as e:
+        P.Instance.from_ilp(g).plan_digest()
+    assert e.value.code == P.FDOG_ESTATE

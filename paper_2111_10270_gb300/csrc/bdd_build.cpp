@@ -11,6 +11,7 @@
 #include <thread>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <unordered_map>
 #include <utility>
@@ -155,6 +156,90 @@ Analysis analyse(const std::vector<int64_t>& a, int8_t sense, int64_t rhs) {
     return an;
 }
 
+// SplitMix64 finaliser (Steele, Lea, Flood 2014) as the mixing step of the row hashes
+inline uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The first presolve pass when it fixes nothing: every row's signature is
+// hashed in parallel, signatures are numbered in order of first occurrence
+// (per-chunk first occurrences merged in chunk order), every row is compared
+// with its signature's first row, and each signature is analysed once.  This
+// is what the sequential pass computes whenever no row forces a variable, is
+// empty or fails; in any of those cases (or on a hash collision) it returns
+// false and the sequential pass runs instead.
+bool first_pass_parallel(int32_t n_rows, const std::vector<int64_t>& rb,
+                         const std::vector<int64_t, DefaultInitAlloc<int64_t>>& ra,
+                         const int8_t* sense, const int64_t* rhs, std::vector<Analysis>& analyses,
+                         std::vector<int>& row_an, std::vector<uint8_t>& alive) {
+    if (n_rows <= 0) return false;
+    std::vector<uint64_t> hash(n_rows);
+    std::atomic<bool> empty{false};
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) {
+            if (rb[j] == rb[j + 1]) empty = true;
+            uint64_t h = mix64(static_cast<uint64_t>(static_cast<int64_t>(sense[j]) + 2));
+            h = mix64(h ^ static_cast<uint64_t>(rhs[j]));
+            h = mix64(h ^ static_cast<uint64_t>(rb[j + 1] - rb[j]));
+            for (int64_t q = rb[j]; q < rb[j + 1]; ++q) h = mix64(h ^ static_cast<uint64_t>(ra[q]));
+            hash[j] = h;
+        }
+    });
+    if (empty) return false;
+    // first occurrences per chunk of rows, merged in row order: ids number the
+    // signatures by first occurrence whatever the chunking
+    std::mutex mu;
+    std::vector<std::pair<int64_t, std::vector<std::pair<uint64_t, int32_t>>>> parts;
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+        std::unordered_map<uint64_t, int32_t> seen;
+        std::vector<std::pair<uint64_t, int32_t>> firsts;
+        for (int64_t j = j0; j < j1; ++j)
+            if (seen.emplace(hash[j], static_cast<int32_t>(j)).second)
+                firsts.emplace_back(hash[j], static_cast<int32_t>(j));
+        std::lock_guard<std::mutex> lk(mu);
+        parts.emplace_back(j0, std::move(firsts));
+    });
+    std::sort(parts.begin(), parts.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    std::unordered_map<uint64_t, int> id_of;
+    std::vector<int32_t> rep;
+    for (const auto& part : parts)
+        for (const auto& [h, j] : part.second)
+            if (id_of.emplace(h, static_cast<int>(rep.size())).second) rep.push_back(j);
+    std::atomic<bool> collision{false};
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) {
+            const int id = id_of.at(hash[j]);
+            const int32_t r = rep[id];
+            row_an[j] = id;
+            if (r == j) continue;
+            bool same = sense[j] == sense[r] && rhs[j] == rhs[r] && rb[j + 1] - rb[j] == rb[r + 1] - rb[r];
+            for (int64_t q = 0; same && q < rb[j + 1] - rb[j]; ++q) same = ra[rb[j] + q] == ra[rb[r] + q];
+            if (!same) collision = true;
+        }
+    });
+    if (collision) return false;
+    analyses.resize(rep.size());
+    std::atomic<bool> presolve{false};
+    parallel_chunks(static_cast<int64_t>(rep.size()), [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            const int32_t j = rep[i];
+            std::vector<int64_t> a(ra.begin() + rb[j], ra.begin() + rb[j + 1]);
+            analyses[i] = analyse(a, sense[j], rhs[j]);
+            if (analyses[i].status != FDOG_OK) { presolve = true; continue; }
+            for (int8_t f : analyses[i].forced)
+                if (f >= 0) presolve = true;
+        }
+    });
+    if (presolve) return false;
+    parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
+        for (int64_t j = j0; j < j1; ++j) alive[j] = analyses[row_an[j]].full_cube ? 0 : 1;
+    });
+    return true;
+}
+
 std::string signature(int8_t sense, int64_t rhs, const std::vector<int64_t>& a) {
     std::string key(1 + 8 + 8 * a.size(), '\0');
     key[0] = static_cast<char>(sense);
@@ -224,8 +309,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         }
     });
     for (int32_t j = 0; j < n_rows; ++j) rb[j + 1] += rb[j];
-    std::vector<int32_t> rv(static_cast<size_t>(rb[n_rows]));
-    std::vector<int64_t> ra(static_cast<size_t>(rb[n_rows]));
+    std::vector<int32_t, DefaultInitAlloc<int32_t>> rv(static_cast<size_t>(rb[n_rows]));  // filled below
+    std::vector<int64_t, DefaultInitAlloc<int64_t>> ra(static_cast<size_t>(rb[n_rows]));
     parallel_chunks(n_rows, [&](int64_t j0, int64_t j1) {
         std::vector<std::pair<int32_t, int32_t>> tmp;
         for (int64_t j = j0; j < j1; ++j) {
@@ -253,7 +338,14 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         }
     };
 
-    for (bool changed = true; changed;) {
+    const bool parallel_done = first_pass_parallel(n_rows, rb, ra, sense, rhs, analyses, row_an, alive);
+    if (!parallel_done) {
+        // the sequential passes below start from scratch
+        analyses.clear();
+        std::fill(row_an.begin(), row_an.end(), -1);
+        std::fill(alive.begin(), alive.end(), 1);
+    }
+    for (bool changed = !parallel_done; changed;) {
         changed = false;
         for (int32_t j = 0; j < n_rows; ++j) {
             if (!alive[j]) continue;
@@ -400,9 +492,24 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
     for (int32_t i = 0; i < n_vars; ++i) out.csr_off[i + 1] = out.csr_off[i] + cnt[i];
     out.n_slots = out.csr_off[n_vars];
     out.csr_pos.resize(out.n_slots);
-    std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
-    for (int64_t p = 0; p < slot; ++p)
-        if (out.var[p] >= 0) out.csr_pos[fill[out.var[p]]++] = static_cast<int32_t>(p);
+    {
+        // scattered in parallel, then each variable's few positions sorted
+        std::vector<int32_t> fill(out.csr_off.begin(), out.csr_off.end() - 1);
+        parallel_chunks(slot, [&](int64_t p0, int64_t p1) {
+            for (int64_t p = p0; p < p1; ++p) {
+                const int32_t v = out.var[p];
+                if (v >= 0) out.csr_pos[__atomic_fetch_add(&fill[v], 1, __ATOMIC_RELAXED)] = static_cast<int32_t>(p);
+            }
+        });
+        parallel_chunks(n_vars, [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                int32_t* q = out.csr_pos.data() + out.csr_off[i];
+                const int32_t c = out.csr_off[i + 1] - out.csr_off[i];
+                for (int32_t x = 1; x < c; ++x)  // insertion sort: a variable has few copies
+                    for (int32_t y = x; y > 0 && q[y - 1] > q[y]; --y) std::swap(q[y - 1], q[y]);
+            }
+        });
+    }
     // Tile-local variables: every copy in one tile (at most four copies) of a
     // row of at most kEpiMaxK layers.  The
     // update sweep computes their deferred term itself; the deferred-sum

@@ -9,7 +9,9 @@
 #include <new>
 #include <thread>
 #include <cstdint>
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/fastdog.h"
@@ -235,6 +237,27 @@ struct Decomposition {
     int32_t* d_bdd_row = nullptr;
 };
 
+// std::allocator whose value-less construct leaves trivial types
+// uninitialised: resize() then costs no fill pass over arrays that are
+// written right after (the instance's copy of the ILP).
+template <class T>
+struct DefaultInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = DefaultInitAlloc<U>;
+    };
+    DefaultInitAlloc() = default;
+    template <class U>
+    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    template <class U>
+    void construct(U* p) noexcept {
+        ::new (static_cast<void*>(p)) U;
+    }
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+    }
+};
 // fn(begin, end) over [0, n) in contiguous chunks on up to 16 host threads.
 // Callers give each chunk independent work and combine any per-chunk results
 // in chunk order, so the plan does not depend on the thread count.

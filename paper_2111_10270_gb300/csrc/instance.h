@@ -13,27 +13,6 @@
 
 namespace fdog {
 
-// std::allocator whose value-less construct leaves trivial types
-// uninitialised: resize() then costs no fill pass over arrays that are
-// written right after (the instance's copy of the ILP).
-template <class T>
-struct DefaultInitAlloc : std::allocator<T> {
-    template <class U>
-    struct rebind {
-        using other = DefaultInitAlloc<U>;
-    };
-    DefaultInitAlloc() = default;
-    template <class U>
-    DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
-    template <class U>
-    void construct(U* p) noexcept {
-        ::new (static_cast<void*>(p)) U;
-    }
-    template <class U, class... A>
-    void construct(U* p, A&&... a) {
-        ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
-    }
-};
 template <class T>
 using HostArray = std::vector<T, DefaultInitAlloc<T>>;
 

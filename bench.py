@@ -72,6 +72,7 @@ def parse():
                     help="requests of the serving stream replayed in the serving section (0: skip)")
     ap.add_argument("--schemes", type=int, default=1, help="update-scheme comparison section (0: skip)")
     ap.add_argument("--split", type=int, default=1, help="long-row splitting section (0: skip)")
+    ap.add_argument("--lb-star", type=int, default=1, help="time to 1e-4 of the stored FP64 LB* (mrf512; 0: skip)")
     ap.add_argument("--threads", type=int, default=min(16, os.cpu_count() or 1),
                     help="host threads / processes for instance generation and planning")
     return ap.parse_args()
@@ -494,6 +495,40 @@ def split_section(torch, P, dev, stream):
     return {"instance": "QAP-shaped matching 500x1000, 20 candidates, 10-NN AND products, seed 2", "cases": cases}
 
 
+LB_STAR_FILE = os.path.join(ROOT, "tests", "golden", "mrf512_lb_star.txt")
+
+
+def lb_star_section(torch, P, g, dev, stream):
+    """Dual iterations and device time the GPU needs to come within 1e-4
+    (relative) of LB*, the FP64 oracle's bound after 2,000 iterations of the
+    same schedule on the 512x512 grid (stored by
+    tests/golden/make_mrf512_lb_star.py); no early stop."""
+    if not os.path.exists(LB_STAR_FILE):
+        return None
+    rec = {}
+    with open(LB_STAR_FILE) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    lb_star, iters = float(rec["lb_star"]), int(rec["iterations"])
+    inst = P.Instance.from_ilp(g, tol=0.0).build(dev, stream)
+    tr = np.array([inst.iterate(1)[1] for _ in range(iters)])
+    hit = np.nonzero(tr >= lb_star - 1e-4 * abs(lb_star))[0]
+    k = int(hit[0]) + 1 if len(hit) else None
+    inst.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    inst.iterate(k or iters)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    inst.close()
+    return {"lb_star": lb_star, "lb_star_source": f"FP64 oracle, {iters} iterations of Alg. 1 (omega 0.5), stored",
+            "iters_to_1e-4": k, "seconds_to_1e-4": t if k else None,
+            "gpu_bound_after_same_iters": float(tr[-1]),
+            "gpu_vs_oracle_rel_diff": abs(float(tr[-1]) - lb_star) / max(1.0, abs(lb_star))}
+
+
 def sweep_traffic(workload):
     """DRAM bytes per update-sweep launch from the committed ncu summary (of
     the 512x512 MRF), if the sweep's generator sources are unchanged since."""
@@ -647,7 +682,12 @@ def main():
                          f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
 
     # ---- batched and served instance mixes (rank 0, N = 1) ---------------------
-    batched = served = schemes = split = None
+    batched = served = schemes = split = lb_star = None
+    if rank == 0 and world == 1 and args.lb_star and args.workload == "mrf512":
+        try:
+            lb_star = lb_star_section(torch, P, g, dev, stream)
+        except Exception as exc:  # a report section: its failure must not cost the bench line
+            lb_star = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and world == 1 and args.schemes:
         schemes = update_scheme_section(P, dev, stream)
     if rank == 0 and world == 1 and args.split:
@@ -671,6 +711,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "batched": batched, "serving": served, "update_schemes": schemes, "long_rows": split,
+            "time_to_lb_star": lb_star,
         }
         print(json.dumps(line), flush=True)
     inst.close()

@@ -30,9 +30,9 @@ def main():
         f.write("# FP64 oracle, Alg. 1 with omega = 0.5, on ilpgen.mrf_grid(512, 512, 4, 1, potts_max=2.0)\n")
         f.write(f"# written by tests/golden/make_mrf512_lb_star.py ({dt:.0f} s single-threaded)\n")
         f.write(f"iterations: {ITERS}\n")
-        f.write(f"lb_star: {tr[-1]!r}\n")
+        f.write(f"lb_star: {float(tr[-1])!r}\n")
         for k in (100, 200, 500, 1000, 1500, 2000):
-            f.write(f"lb_after_{k}: {tr[k - 1]!r}\n")
+            f.write(f"lb_after_{k}: {float(tr[k - 1])!r}\n")
     print(open(out).read())
 
 

@@ -48,8 +48,8 @@ WORKLOADS = {
                   desc="cell-tracking instance (first of the seed-3 batch): frames U{10..80}, "
                        "detections/frame U{200..2000}"),
 }
-METRIC = ("BDD arc-updates/s (full FastDOG solve: up to 500 dual iterations, stopping early at the 1e-4 LB-gap rule, "
-          "+ perturbation rounding)")
+METRIC = ("BDD arc-updates/s (full FastDOG solve: dual iterations up to the workload's cap, 500 on the 512x512 grid, "
+          "stopping early at the 1e-4 LB-gap rule, + perturbation rounding)")
 UNIT = "arc-updates/s"
 SWEEP_SRCS = [os.path.join(ROOT, "paper_2111_10270_gb300", "csrc", f)
               for f in ("jit.cpp", "jit_skeleton.cuh", "kernels.cu")]  # generator, skeleton, launch (L2 window)

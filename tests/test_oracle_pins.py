@@ -600,3 +600,22 @@ def test_energies_sum_to_the_running_bound(oracle_mod):
     assert abs(p.energies().sum() + p.const_lb - run) < 1e-12
     hi, lo, _, _ = p.state()
     assert abs(p.energies().sum() + p.const_lb - lifted_energy_bruteforce(p, ilp, hi, lo)) < 1e-9
+
+
+def test_stored_lb_star_trajectory_is_monotone():
+    """The stored 2,000-iteration oracle bound of the 512x512 grid (written by
+    tests/golden/make_mrf512_lb_star.py): the lifted bound never decreases
+    (Prop. 1), and LB* is the bound after the last iteration."""
+    import os
+
+    rec = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "mrf512_lb_star.txt")) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    its = [100, 200, 500, 1000, 1500, 2000]
+    tr = [float(rec[f"lb_after_{k}"]) for k in its]
+    assert int(rec["iterations"]) == 2000
+    assert all(b >= a for a, b in zip(tr, tr[1:]))
+    assert float(rec["lb_star"]) == tr[-1]

@@ -25,7 +25,8 @@
  *     the legacy default stream.  All device work of an instance is ordered on
  *     the stream given to fdog_build_bdds.
  *   - Floating point: sweeps, multipliers and min-marginals are FP32; lower
- *     bounds and objectives are reduced in FP64 with compensated summation.
+ *     bounds and objectives are reduced in FP64 with compensated summation,
+ *     and a bound evaluated at a given state uses FP64 labels.
  */
 #ifndef FASTDOG_H
 #define FASTDOG_H
@@ -296,7 +297,12 @@ int fdog_finalize(fdog_instance* inst);
  *                  differences back (Alg. 1, last loop), i.e. at dual-feasible
  *                  multipliers with sum_j lambda^j_i = c_i.
  * Both include the constant of variables fixed by presolve or in no row.
- * Either pointer may be NULL.  Does not modify the state.
+ * *lb_feasible (and *lb_running when no iteration has run since the state was
+ * last set) is evaluated with FP64 shortest-path labels over the FP32
+ * multipliers and summed with FP64 Neumaier in a fixed order; *lb_running
+ * after iterations is the bound the last iteration reduced (FP32 per-BDD
+ * energies, compensated sums).  Either pointer may be NULL.  Does not modify
+ * the state.
  */
 int fdog_lower_bound(fdog_instance* inst, double* lb_running, double* lb_feasible);
 
@@ -453,14 +459,18 @@ void fdog_server_destroy(fdog_server* srv);
  * loops that forbid allocation after start-up).
  * Writes to dev_out[0] the deterministic FP64 compensated sum
  * constant + sum_{t < n} dev_values[t] -- e.g. per-subproblem energies E_j, so
- * that the result is the bound sum_j E^j of Eq. D -- using the same fixed
- * chunking as the library's own bound reduction.  dev_values (n doubles) and
- * dev_out (one double) are device memory owned by the caller; the call
- * allocates nothing: its scratch is a static device array of 256 KiB that
- * every GPU loading this library holds until the process exits.
+ * that the result is the bound sum_j E^j of Eq. D -- with the same two-stage
+ * compensated reduction as the library's own bound kernels: per-block
+ * partials (256 values per block), then a last-block Neumaier sum of them.
+ * dev_values (n doubles) and dev_out (one double) are device memory owned by
+ * the caller; the call allocates nothing: its scratch is a static device
+ * array of 256 KiB that every GPU loading this library holds until the
+ * process exits.  n = 0 writes `constant`.
  * n may be at most 8,388,608 (FDOG_EINVAL beyond, or for negative n or NULL
  * pointers).  The first call on a device looks up that array's device address
- * with the device current; make that first call before any stream capture.
+ * with the device current, and so does the first call after cudaDeviceReset
+ * (the address is cached per device and context); make those calls before
+ * any stream capture.
  * Work is queued on cuda_stream (NULL: legacy default stream); the call does
  * not wait for it.  All calls share the one scratch array, so calls whose
  * kernels overlap on the GPU (different streams, or several host threads)

@@ -477,10 +477,10 @@ int set_ctl_field(fdog_instance* inst, size_t offset, const void* v, size_t byte
     return e == cudaSuccess ? FDOG_OK : fail_cuda(inst, e, "write control block");
 }
 
-// Energy sum (+ presolve constant) at lambda, or at lambda + T (the add-back).
+// Energy sum (+ presolve constant) at lambda, or at lambda + T (the add-back),
+// with FP64 shortest-path labels and FP64 compensated sums (eval.cu).
 int evaluate(fdog_instance* inst, bool add_t, double* out) {
-    cudaError_t e = launch_sweep(inst->batch, kEval, add_t ? kMMAddT : 0, inst->cfg, inst->stream);
-    if (e == cudaSuccess) e = launch_lb_reduce(inst->batch, kLbEval, inst->cfg, inst->stream);
+    cudaError_t e = launch_eval64(inst->batch, add_t, inst->cfg, inst->stream);
     if (e != cudaSuccess) return fail_cuda(inst, e, "evaluate");
     InstCtl c;
     int rc = read_ctl(inst, c);

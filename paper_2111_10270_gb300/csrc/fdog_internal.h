@@ -81,7 +81,7 @@ struct TileDev {
 struct InstCtl {
     double lb_ring[FDOG_LB_RING];  // running lower bound after iteration t at [t % kLbRing]
     double lb_last;           // running lower bound after the last iteration
-    double lb_eval;           // result of the last evaluation reduction
+    double lb_eval;           // result of the last FP64 evaluation (eval.cu)
     double objective;         // c^T x of the last rounding (without presolve constants)
     int32_t iter;             // dual iterations completed since the build
     int32_t done;             // stopping rule met: update kernels become no-ops

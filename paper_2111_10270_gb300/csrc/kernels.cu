@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     InstCtl* ctl = I->ctl;
-    if (a.target != kLbEval && FDOG_INACTIVE(ctl)) return;
+    if (FDOG_INACTIVE(ctl)) return;
     const int c = g - __ldg(a.prefix + ii);
     const int t = c * kLbChunk + threadIdx.x;
     // the chunk's tile partials as compensated FP32 pairs (FP64 is a small
@@ -221,12 +221,8 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
         neumaier(S, Cc, I->const_lb);
         const double lb = S + Cc;
         ctl->ticket = 0;
-        if (a.target == kLbStage) {
-            ctl->lb_staged = lb;
-            ctl->staged = 1;
-        } else {
-            ctl->lb_eval = lb;
-        }
+        ctl->lb_staged = lb;
+        ctl->staged = 1;
     }
 }
 

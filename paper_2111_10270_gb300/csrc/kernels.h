@@ -21,9 +21,9 @@ enum SweepMode : int {
 constexpr int kMMAddT = 1;   // evaluate at lambda + T (the add-back of Alg. 1)
 constexpr int kMMBoth = 2;   // write m0 and m1 (else M = m1 - m0 into mm0)
 
-// lower-bound reduction targets
-constexpr int kLbEval = 1;     // evaluation: InstCtl::lb_eval
-constexpr int kLbStage = 2;    // bound of an iteration into InstCtl::lb_staged (committed later)
+// lower-bound reduction target: the bound of an iteration into InstCtl::lb_staged (committed later);
+// evaluations at a given state use launch_eval64
+constexpr int kLbStage = 2;
 
 constexpr int kLbChunk = FDOG_LB_CHUNK;  // tiles per chunk of the lower-bound reduction
 constexpr int kObjChunk = 8192;  // variables per block of the objective reduction
@@ -136,6 +136,9 @@ int smem_max_layers(int width);
 cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s);
+// FP64 evaluation of every member's bound sum_j E^j at lambda (or lambda + T
+// with add_t) into InstCtl::lb_eval (eval.cu)
+cudaError_t launch_eval64(const DevBatch& b, bool add_t, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_init(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_addback(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_zero_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);

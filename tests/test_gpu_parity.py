@@ -73,6 +73,31 @@ def test_fig2_first_iteration_matches_oracle_exactly(P, oracle_mod):
 # ----------------------------------------------------------------------------
 # trajectory and evaluation parity
 # ----------------------------------------------------------------------------
+def mm_parity(orc, inst):
+    """Every slot's m0 and m1 and their difference against the oracle's (the
+    oracle's state must be the one to compare with)."""
+    var, row, m0, m1 = inst.min_marginals()
+    om0, om1 = orc.min_marginals()
+    perm = slot_order(orc, var, row)
+    e0, e1 = rel_err(m0[perm], om0).max(), rel_err(m1[perm], om1).max()
+    ed = rel_err(m1[perm] - m0[perm], om1 - om0).max()
+    assert e0 <= MM_RTOL and e1 <= MM_RTOL and ed <= MM_RTOL, (e0, e1, ed)
+    return max(e0, e1, ed)
+
+
+def evaluation_parity(orc, inst):
+    """The oracle evaluates the GPU's finalised multipliers: the feasible bound
+    within 1e-6 max(1, |LB|) and every slot's min-marginals within 1e-4."""
+    inst.finalize()
+    var, row, lam = inst.multipliers()
+    orc.set_state(lam[slot_order(orc, var, row)].astype(np.float64))
+    run, fea = inst.lower_bound()
+    orun, ofea = orc.lower_bounds()
+    assert lb_close(fea, ofea), (fea, ofea)
+    assert lb_close(run, orun), (run, orun)
+    return abs(fea - ofea) / max(1.0, abs(ofea)), mm_parity(orc, inst)
+
+
 def trajectory(P, oracle_mod, ilp, iters, omega=0.5, jit=1):
     """Same schedule on both sides; also returns the oracle's sum_j |E_j| after
     every iteration (the conditioning of the bound as a sum)."""
@@ -144,10 +169,8 @@ def test_random_ilp_trajectory_parity(P, oracle_mod, seed, jit):
     # FP32 trajectories of a sum with cancellation: relative to sum_j |E_j|
     bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    mm_parity(orc, inst)
+    evaluation_parity(orc, inst)
 
 
 @pytest.mark.parametrize("jit", [1, -1], ids=["specialised", "generic"])
@@ -188,10 +211,8 @@ def test_wide_and_long_rows_parity(P, oracle_mod, jit):
     # FP32 trajectories of a sum with cancellation: relative to sum_j |E_j|
     bad = [t for t in range(40) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    mm_parity(orc, inst)
+    evaluation_parity(orc, inst)
 
 
 @pytest.mark.parametrize("jit", [1, 0], ids=["specialised", "auto"])
@@ -209,10 +230,8 @@ def test_qap_and_cell_tracking_parity(P, oracle_mod, kind, jit):
         assert counts.max() > 8, counts.max()
     bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL, kp
+    mm_parity(orc, inst)
+    evaluation_parity(orc, inst)
 
 
 def serial_cases():
@@ -237,12 +256,9 @@ def test_serial_update_parity(P, oracle_mod, kind):
         cond.append(np.abs(orc.energies()).sum())
     bad = [t for t in range(iters) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    mm_parity(orc, inst)
     # every copy sum still equals the cost (Eq. 4 only redistributes)
-    _, _, lam = inst.multipliers()
+    var, _, lam = inst.multipliers()
     sums = np.bincount(var, lam.astype(np.float64), minlength=g.n_vars)
     inb = np.bincount(var, minlength=g.n_vars) > 0
     assert np.abs(sums - np.asarray(g.cost))[inb].max() <= 1e-4 * max(1.0, np.abs(g.cost).max())
@@ -305,10 +321,8 @@ def test_split_rows_parity(P, oracle_mod, kind):
     inst, orc, gl, ol, cond = trajectory(P, oracle_mod, s, 40)
     bad = [t for t in range(len(gl)) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
+    mm_parity(orc, inst)
+    evaluation_parity(orc, inst)
     if kind == "qap":
         assert np.diff(s.row_ptr).max() <= max_len
 
@@ -333,17 +347,8 @@ def test_long_narrow_rows_parity(P, oracle_mod, jit):
         cond.append(np.abs(orc.energies()).sum())
     bad = [t for t in range(iters) if not lb_close(gl[t], ol[t], scale=cond[t])]
     assert not bad, [(t, gl[t], ol[t], cond[t]) for t in bad[:4]]
-    var, row, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm = slot_order(orc, var, row)
-    assert rel_err(m1[perm] - m0[perm], om1 - om0).max() <= MM_RTOL
-    inst.finalize()
-    var, row, lam = inst.multipliers()
-    perm = slot_order(orc, var, row)
-    orc.set_state(lam[perm].astype(np.float64))
-    run, fea = inst.lower_bound()
-    _, ofea = orc.lower_bounds()
-    assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum())
+    mm_parity(orc, inst)
+    evaluation_parity(orc, inst)
 
 
 # ----------------------------------------------------------------------------
@@ -525,18 +530,7 @@ def test_qap_evaluation_parity_full_size(P, oracle_mod):
     assert (info["n_vars"], info["n_slots"]) == (1166481, 8115367)
     n, _ = inst.iterate(25)
     assert n == 25
-    inst.finalize()
-    var, row, lam = inst.multipliers()
-    orc = oracle_mod.Problem.from_ilp(g)
-    perm = slot_order(orc, var, row)
-    orc.set_state(lam[perm].astype(np.float64))
-    _, fea = inst.lower_bound()
-    _, ofea = orc.lower_bounds()
-    assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum()), (fea, ofea)
-    var2, row2, m0, m1 = inst.min_marginals()
-    om0, om1 = orc.min_marginals()
-    perm2 = slot_order(orc, var2, row2)
-    assert rel_err(m1[perm2] - m0[perm2], om1 - om0).max() <= MM_RTOL
+    evaluation_parity(oracle_mod.Problem.from_ilp(g), inst)
 
 
 def test_cell_batch_members_parity_full_size(P, oracle_mod):
@@ -550,19 +544,7 @@ def test_cell_batch_members_parity_full_size(P, oracle_mod):
     iters, _, _ = batch.solve(500)
     assert np.all(iters > 0)
     for q in (0, 31, 63):
-        g, inst = ilps[q], insts[q]
-        inst.finalize()
-        var, row, lam = inst.multipliers()
-        orc = oracle_mod.Problem.from_ilp(g)
-        perm = slot_order(orc, var, row)
-        orc.set_state(lam[perm].astype(np.float64))
-        _, fea = inst.lower_bound()
-        _, ofea = orc.lower_bounds()
-        assert lb_close(fea, ofea, scale=np.abs(orc.energies()).sum()), (q, fea, ofea)
-        var2, row2, m0, m1 = inst.min_marginals()
-        om0, om1 = orc.min_marginals()
-        perm2 = slot_order(orc, var2, row2)
-        assert rel_err(m1[perm2] - m0[perm2], om1 - om0).max() <= MM_RTOL, q
+        evaluation_parity(oracle_mod.Problem.from_ilp(ilps[q]), insts[q])
     batch.close()
 
 

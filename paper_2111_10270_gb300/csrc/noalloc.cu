@@ -8,10 +8,12 @@
 // device and has no latency bound).  They already hold the per-subproblem
 // energies E_j in their own device buffer and only need the deterministic
 // compensated sum.  This entry
-// point runs the same per-chunk + last-block reduction as the library's
-// lower-bound kernel, but keeps its scratch -- the chunk partials and the
-// last-block ticket -- in one file-scope static device array instead of memory
-// owned by an instance.
+// point uses the same two-stage compensated reduction as the library's
+// lower-bound kernels -- per-block partials, then a Neumaier sum of them by
+// the last block -- over FP64 inputs, 256 values per block, and keeps its
+// scratch -- the block partials and the last-block ticket -- in one
+// file-scope static device array instead of memory owned by an instance.
+#include <cuda.h>  // CUcontext / CUresult types of the two driver calls fetched at run time
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -37,7 +39,9 @@ struct Scratch {
 static __device__ __align__(256) Scratch g_scratch;
 
 std::mutex g_mu;
+// per device: the scratch address and the id of the context it was looked up in
 Scratch* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
     const double t = s + x;
@@ -86,7 +90,41 @@ __global__ void __launch_bounds__(kChunk) bound_reduce_noalloc_kernel(const doub
     }
 }
 
-// Device address of g_scratch on the current device (set up on first use).
+// Unique id of the calling thread's current CUDA context (0 if there is
+// none), from cuCtxGetCurrent / cuCtxGetId fetched through the runtime, so
+// the library needs no link against the driver library.  The id changes when
+// cudaDeviceReset destroys a device's primary context and a later call
+// creates a new one, in which the module -- and g_scratch -- may be loaded at
+// another address.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_scratch on the current device.  Set-up (the
+// cudaGetSymbolAddress lookup, with the device current) runs on the first
+// call on a device and again whenever the current context is not the one the
+// cached address was looked up in (after cudaDeviceReset).
 Scratch* scratch_for_current_device(int* status) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -95,15 +133,18 @@ Scratch* scratch_for_current_device(int* status) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);  // creates the primary context if needed
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            g_addr[dev] = nullptr;
             *status = FDOG_ECUDA;
             return nullptr;
         }
         g_addr[dev] = static_cast<Scratch*>(p);
+        g_ctx[dev] = current_context_id();
     }
     *status = FDOG_OK;
     return g_addr[dev];

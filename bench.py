@@ -622,9 +622,12 @@ def main():
     S = info["n_slots"]
     n_bdds = info["n_bdds"]
     tiles = kp["jit_tiles"] + kp["static_tiles"]
-    # per sweep launch: per slot lambda read + write, variable id, deferred-term gather (16 B); per tile its
-    # descriptor and bound partial (40 B); per tile-local variable its target C and new deferred term (8 B)
-    alg_bytes = 16 * S + 40 * tiles + 8 * kp["local_vars"]
+    n_row_vars = kp["local_vars"] + kp["work_vars"]  # variables inside some BDD
+    # compulsory bytes of one sweep launch, every array element counted once: per slot lambda read + write
+    # and its variable id (12 B); per variable in a row its deferred term T, read once (4 B; the per-slot
+    # gathers of T beyond the first are re-reads the L2 serves); per tile its descriptor and bound partial
+    # (40 B); per tile-local variable its target C and new deferred term (8 B)
+    alg_bytes = 12 * S + 4 * n_row_vars + 40 * tiles + 8 * kp["local_vars"]
     # per deferred-sum launch: per listed variable its id, C and the new T (12 B); per copy its slot
     # position and the gathered multiplier (8 B)
     reduce_bytes = 12 * kp["work_vars"] + 8 * kp["work_slots"]
@@ -637,9 +640,14 @@ def main():
         peak = 6800.0
     kernel_name = ("fdog_jit_fwd / fdog_jit_bwd (shape-specialised update sweeps)" if kp["jit_tiles"] * 2 >= tiles
                    else "update sweeps of the dominant kernel class")
+    traffic = sweep_traffic(args.workload)
+    dram_gbs = traffic / sweep_avg_s / 1e9 if (traffic and sweep_avg_s > 0) else None
     roofline = {"bound": "hbm", "kernel": kernel_name,
                 "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": sweep_traffic(args.workload),
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_source": (f"{os.path.relpath(TRAFFIC_FILE, ROOT)} (ncu capture of this sweep source, "
+                                   "not measured in this run)") if traffic else None,
+                "dram_achieved": dram_gbs, "dram_frac": dram_gbs / peak if dram_gbs else None,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_us": sweep_avg_s * 1e6,
                 "launches": prof["sweep_launches"],
                 "deferred_sum_kernel": {"avg_launch_us": reduce_avg_s * 1e6, "alg_bytes_per_launch": reduce_bytes,

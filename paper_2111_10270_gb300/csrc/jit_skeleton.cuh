@@ -35,7 +35,9 @@ __device__ __forceinline__ void fdog_tile_local_sums(const InstDev* __restrict__
         if (o.z != 0xFFFFu) { s += ep_lam[o.z]; ++c; }
         if (o.w != 0xFFFFu) { s += ep_lam[o.w]; ++c; }
         const int v = ep_var[o.x];
-        I->T[v] = (I->C[v] - s) / (float)c;
+        // (C - sum) times 1 / c rounded to FP32, as in the deferred-sum kernel
+        const float inv = c == 1 ? 1.f : c == 2 ? 0.5f : c == 3 ? 1.f / 3.f : 0.25f;
+        I->T[v] = (I->C[v] - s) * inv;
     }
 }
 
@@ -83,18 +85,20 @@ __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
             fdog_tile_local_sums(I, tile.pattern, ep_lam, ep_var, lane);
             __syncwarp();
         }
-        float s = valid ? term : 0.f, comp = 0.f;
+        if (MODE == 1 || MODE == 3) {  // only the descending pass and the energy sweep feed a bound reduction
+            float s = valid ? term : 0.f, comp = 0.f;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float o = __shfl_xor_sync(FDOG_FULL, s, off);
-            const float oc = __shfl_xor_sync(FDOG_FULL, comp, off);
-            const float sum = s + o;
-            const float bp = sum - s;
-            const float err = (s - (sum - bp)) + (o - bp);
-            s = sum;
-            comp = comp + oc + err;
+            for (int off = 16; off > 0; off >>= 1) {
+                const float o = __shfl_xor_sync(FDOG_FULL, s, off);
+                const float oc = __shfl_xor_sync(FDOG_FULL, comp, off);
+                const float sum = s + o;
+                const float bp = sum - s;
+                const float err = (s - (sum - bp)) + (o - bp);
+                s = sum;
+                comp = comp + oc + err;
+            }
+            if (lane == 0) I->tile_lb[ti] = make_float2(s, comp);
         }
-        if (lane == 0) I->tile_lb[ti] = make_float2(s, comp);
     }
 }
 

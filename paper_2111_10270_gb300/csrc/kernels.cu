@@ -65,7 +65,7 @@ __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
 #pragma unroll
     for (int q = 0; q < FDOG_WBUCKETS - 1; ++q)
         if (q < cnt) s += l[q];
-    I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
+    I->T[i] = (I->C[i] - s) * dev::inv_copies(cnt);
 }
 
 __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
     for (int q = lane; q < cnt; q += 32) s += lam[__ldcs(pos + q)];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) I->T[i] = (I->C[i] - s) / static_cast<float>(cnt);
+    if (lane == 0) I->T[i] = (I->C[i] - s) * __frcp_rn(static_cast<float>(cnt));  // 1 / cnt rounded to FP32
 }
 
 __device__ __forceinline__ void neumaier(double& s, double& c, double x) {

@@ -89,6 +89,14 @@ struct Store<W, false> {
 };
 
 
+// 1 / c rounded to FP32 for a copy count c <= 8 (constants folded at compile
+// time); the deferred term of a variable is (C_i - sum_j lambda^j_i) times it
+// in every kernel that forms one, so all of them agree bit for bit
+__device__ __forceinline__ float inv_copies(int c) {
+    return c == 1 ? 1.f : c == 2 ? 0.5f : c == 3 ? 1.f / 3.f : c == 4 ? 0.25f
+         : c == 5 ? 1.f / 5.f : c == 6 ? 1.f / 6.f : c == 7 ? 1.f / 7.f : 0.125f;
+}
+
 // Deferred terms of the tile-local variables (every copy in this tile),
 // formed right after the pass from the staged multipliers: the same sum, in
 // the same ascending slot order, as the deferred-sum kernel uses.
@@ -104,7 +112,7 @@ __device__ __forceinline__ void tile_local_sums(const InstDev* __restrict__ I, i
         if (o.z != 0xFFFFu) { s += ep_lam[o.z]; ++c; }
         if (o.w != 0xFFFFu) { s += ep_lam[o.w]; ++c; }
         const int v = ep_var[o.x];
-        I->T[v] = (I->C[v] - s) / static_cast<float>(c);
+        I->T[v] = (I->C[v] - s) * inv_copies(c);
     }
 }
 
@@ -324,19 +332,22 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
             }
         }
 
-        // per-tile partial of the bound: compensated FP32 butterfly (all lanes end equal)
-        float s = valid ? term : 0.f, comp = 0.f;
+        // per-tile partial of the bound: compensated FP32 butterfly (all lanes end equal); only the
+        // descending update pass and the energy sweep feed a bound reduction
+        if constexpr (MODE == kBwdUpdate || MODE == kEval) {  // the passes whose bound is reduced
+            float s = valid ? term : 0.f, comp = 0.f;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float o = __shfl_xor_sync(kFull, s, off);
-            const float oc = __shfl_xor_sync(kFull, comp, off);
-            const float sum = s + o;
-            const float bp = sum - s;
-            const float err = (s - (sum - bp)) + (o - bp);
-            s = sum;
-            comp = comp + oc + err;
+            for (int off = 16; off > 0; off >>= 1) {
+                const float o = __shfl_xor_sync(kFull, s, off);
+                const float oc = __shfl_xor_sync(kFull, comp, off);
+                const float sum = s + o;
+                const float bp = sum - s;
+                const float err = (s - (sum - bp)) + (o - bp);
+                s = sum;
+                comp = comp + oc + err;
+            }
+            if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
         }
-        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
     }
 }
 
@@ -668,18 +679,20 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
             }
         }
 
-        float s = valid ? term : 0.f, comp = 0.f;
+        if constexpr (MODE == kBwdUpdate || MODE == kEval) {  // the passes whose bound is reduced
+            float s = valid ? term : 0.f, comp = 0.f;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float o = __shfl_xor_sync(kFull, s, off);
-            const float oc = __shfl_xor_sync(kFull, comp, off);
-            const float sum = s + o;
-            const float bp = sum - s;
-            const float err = (s - (sum - bp)) + (o - bp);
-            s = sum;
-            comp = comp + oc + err;
+            for (int off = 16; off > 0; off >>= 1) {
+                const float o = __shfl_xor_sync(kFull, s, off);
+                const float oc = __shfl_xor_sync(kFull, comp, off);
+                const float sum = s + o;
+                const float bp = sum - s;
+                const float err = (s - (sum - bp)) + (o - bp);
+                s = sum;
+                comp = comp + oc + err;
+            }
+            if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
         }
-        if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
     }
 }
 

@@ -453,6 +453,82 @@ const char* fdog_server_last_error(const fdog_server* srv);
 void fdog_server_destroy(fdog_server* srv);
 
 /*
+ * One instance split over several GPUs (the paper's conclusion names
+ * multi-GPU support as future work).  Within one pass of Alg. 1 the BDDs are
+ * independent (Eq. 5 reads only a BDD's own multipliers and the deferred
+ * terms of the previous pass); they are coupled only through the deferred
+ * term T_i = (c_i - sum_j lambda^j_i) / |J_i| (Prop. 1), a sum over every copy
+ * of variable i.  So the rows are split into shards, each an ordinary
+ * instance of its own rows (one process and one GPU per shard), and once per
+ * pass the shards all-reduce one float per variable whose copies lie in
+ * several shards, and once per iteration the lower bound.  The all-reduce is
+ * the caller's (NCCL or any other); these calls produce and consume the
+ * per-shard sums on the instance's stream.  Rounding (Alg. 2) is not run on
+ * shards.
+ *
+ * fdog_shard_plan (host only): splits rows 0..n_rows-1 of an ILP in the
+ * fdog_create form into n_shards contiguous blocks with about equal numbers
+ * of non-zero entries: row_shard[j] (n_rows), copies[i] = |J_i|, the rows
+ * with a non-zero coefficient on variable i (n_vars), shared[i] = 1 when
+ * rows of more than one shard hold i (n_vars).  coef may be NULL (every entry
+ * counts).  FDOG_EINVAL on a malformed CSR or n_shards < 1.
+ *
+ * fdog_shard_setup: marks a created, unplanned instance as one shard.  Its
+ * ILP is the whole ILP's variables (same n_vars) with this shard's rows; a
+ * variable with no row in the shard should carry cost 0 there (its cost
+ * belongs to the shards that hold it, or to one shard if no row holds it).
+ * shared / copies are the arrays fdog_shard_plan wrote.  The plan is built on
+ * the host and must need no presolve (FDOG_EUNSUPPORTED otherwise, at build).
+ * FDOG_ESTATE if already planned; FDOG_EUNSUPPORTED for update = 1.
+ * fdog_shard_info: *n_shared = the number of shared variables of the split
+ * instance (sum of shared[]), the length of the exchange buffer, the same on
+ * every shard; entry k belongs to the k-th shared variable in ascending
+ * index order.  Plans the instance if needed.
+ *
+ * One iteration of Alg. 1 over all shards, on every shard:
+ *   fdog_shard_pass(inst, 0, dev_sums)   ascending pass over the shard's BDDs,
+ *                                        deferred terms of its unshared
+ *                                        variables, dev_sums[k] = this shard's
+ *                                        sum of lambda over the k-th shared
+ *                                        variable's copies, 0 where it holds
+ *                                        none (device memory of n_shared
+ *                                        floats, caller-owned)
+ *   all-reduce (sum) dev_sums over the shards
+ *   fdog_shard_apply(inst, dev_sums)     T_i of the shared variables
+ *   fdog_shard_pass(inst, 1, dev_sums)   the same for the descending pass; it
+ *                                        also reduces the shard's part of the
+ *                                        lower bound
+ *   all-reduce dev_sums, fdog_shard_apply
+ *   fdog_shard_bound(inst, &part)        (waits) this shard's part: the lifted
+ *                                        energies of its BDDs plus its
+ *                                        presolve constant
+ *   all-reduce (sum) part
+ *   fdog_shard_commit(inst, lb, &stop)   (waits) records the iteration's bound
+ *                                        and runs the stopping rule; *stop = 1
+ *                                        when it fired (every shard given the
+ *                                        same bound decides the same)
+ * Work is queued on the instance's stream; an all-reduce must be ordered
+ * after the pass and before the apply on that stream.  fdog_finalize,
+ * fdog_lower_bound, fdog_min_marginals and fdog_multipliers work on a shard
+ * and describe its own BDDs: its bounds are this shard's part, except
+ * lb_running after iterations, which is the last committed bound of the
+ * whole instance.
+ * fdog_dual_iterate returns FDOG_ESTATE on a shard; fdog_primal_round,
+ * batches and servers refuse shards (FDOG_EUNSUPPORTED).  Errors:
+ * FDOG_EINVAL (NULL buffer with shared variables, bad direction),
+ * FDOG_ESTATE (not a shard, not built, no descending pass before
+ * fdog_shard_bound), FDOG_ECUDA.
+ */
+int fdog_shard_plan(int32_t n_vars, int32_t n_rows, const int64_t* row_ptr, const int32_t* col, const int32_t* coef,
+                    int32_t n_shards, int32_t* row_shard, int32_t* copies, uint8_t* shared);
+int fdog_shard_setup(fdog_instance* inst, const uint8_t* shared, const int32_t* copies);
+int fdog_shard_info(fdog_instance* inst, int32_t* n_shared);
+int fdog_shard_pass(fdog_instance* inst, int32_t descending, float* dev_sums);
+int fdog_shard_apply(fdog_instance* inst, const float* dev_sums);
+int fdog_shard_bound(fdog_instance* inst, double* lb_part);
+int fdog_shard_commit(fdog_instance* inst, double lb, int32_t* stop);
+
+/*
  * Allocation-free lower-bound reduction (the paper has no counterpart: this
  * serves callers that cannot allocate device memory -- plug-ins whose host
  * framework owns every device allocation through its own pool, and real-time

@@ -105,6 +105,13 @@ SIGNATURES = {
                                           ctypes.POINTER(_i64), ctypes.POINTER(_f64), ctypes.POINTER(_i64)]),
     "fdog_server_last_error": (ctypes.c_char_p, [_P]),
     "fdog_server_destroy": (None, [_P]),
+    "fdog_shard_plan": (ctypes.c_int, [_i32, _i32, _P, _P, _P, _i32, _P, _P, _P]),
+    "fdog_shard_setup": (ctypes.c_int, [_P, _P, _P]),
+    "fdog_shard_info": (ctypes.c_int, [_P, ctypes.POINTER(_i32)]),
+    "fdog_shard_pass": (ctypes.c_int, [_P, _i32, _P]),
+    "fdog_shard_apply": (ctypes.c_int, [_P, _P]),
+    "fdog_shard_bound": (ctypes.c_int, [_P, ctypes.POINTER(_f64)]),
+    "fdog_shard_commit": (ctypes.c_int, [_P, _f64, ctypes.POINTER(_i32)]),
     "fdog_bound_reduce_noalloc": (ctypes.c_int, [_P, _i64, _f64, _P, _P]),
     "fdog_last_error": (ctypes.c_char_p, [_P]),
     "fdog_destroy": (None, [_P]),
@@ -170,6 +177,23 @@ def split_rows(n_vars, row_ptr, col, coef, sense, rhs, max_len: int):
         raise FdogError(rc, "fdog_split_rows")
     m, k = nr.value, nnz.value
     return nv.value, o_ptr, o_col[:k], o_coef[:k], o_sense[:m], o_rhs[:m], o_orig[:m]
+
+
+def shard_plan(n_vars, row_ptr, col, coef, n_shards: int):
+    """fdog_shard_plan: (row_shard, copies, shared) of the rows split into
+    n_shards contiguous blocks with about equal numbers of non-zero entries."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    coef = np.ascontiguousarray(coef, np.int32)
+    n_rows = len(row_ptr) - 1
+    row_shard = np.zeros(max(n_rows, 1), np.int32)
+    copies = np.zeros(max(int(n_vars), 1), np.int32)
+    shared = np.zeros(max(int(n_vars), 1), np.uint8)
+    rc = lib().fdog_shard_plan(int(n_vars), n_rows, _ptr(row_ptr), _ptr(col), _ptr(coef), int(n_shards),
+                               _ptr(row_shard), _ptr(copies), _ptr(shared))
+    if rc != FDOG_OK:
+        raise FdogError(rc, "fdog_shard_plan")
+    return row_shard[:n_rows], copies[:n_vars], shared[:n_vars]
 
 
 def default_params(**kw) -> Params:
@@ -360,6 +384,36 @@ class Instance:
     def import_state(self, blob: bytes):
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._check(self._L.fdog_import_state(self._h, buf, len(blob)), "fdog_import_state")
+
+    # ---- one shard of a split instance (see fastdog.h, fdog_shard_*) ----
+    def shard_setup(self, shared, copies):
+        shared = np.ascontiguousarray(shared, np.uint8)
+        copies = np.ascontiguousarray(copies, np.int32)
+        assert len(shared) == self.n_vars and len(copies) == self.n_vars
+        self._check(self._L.fdog_shard_setup(self._h, _ptr(shared), _ptr(copies)), "fdog_shard_setup")
+        return self
+
+    def shard_info(self) -> int:
+        n = _i32()
+        self._check(self._L.fdog_shard_info(self._h, ctypes.byref(n)), "fdog_shard_info")
+        return n.value
+
+    def shard_pass(self, descending: bool, dev_sums: int):
+        self._check(self._L.fdog_shard_pass(self._h, 1 if descending else 0, ctypes.c_void_p(dev_sums)),
+                    "fdog_shard_pass")
+
+    def shard_apply(self, dev_sums: int):
+        self._check(self._L.fdog_shard_apply(self._h, ctypes.c_void_p(dev_sums)), "fdog_shard_apply")
+
+    def shard_bound(self) -> float:
+        v = _f64()
+        self._check(self._L.fdog_shard_bound(self._h, ctypes.byref(v)), "fdog_shard_bound")
+        return v.value
+
+    def shard_commit(self, lb: float) -> bool:
+        stop = _i32()
+        self._check(self._L.fdog_shard_commit(self._h, float(lb), ctypes.byref(stop)), "fdog_shard_commit")
+        return bool(stop.value)
 
     def info(self):
         v = [_i64() for _ in range(5)]

@@ -90,6 +90,9 @@ static std::vector<Item> arena_items(const fdog_instance* inst, DevArrays& a) {
         {reinterpret_cast<void**>(&a.chunk_lb), sizeof(double) * static_cast<size_t>(nchunks)},
         {reinterpret_cast<void**>(&a.obj_chunk), sizeof(double) * static_cast<size_t>(nobj)},
         {reinterpret_cast<void**>(&a.prefix), sizeof(int32_t) * kPrefixInts},
+        {reinterpret_cast<void**>(&a.sh_vars), sizeof(int32_t) * std::max<size_t>(d.shared_vars.size(), 1)},
+        {reinterpret_cast<void**>(&a.sh_copies), sizeof(int32_t) * std::max<size_t>(d.shared_vars.size(), 1)},
+        {reinterpret_cast<void**>(&a.sh_slot), sizeof(int32_t) * std::max<size_t>(d.shared_vars.size(), 1)},
     };
 }
 
@@ -126,13 +129,14 @@ int plan(fdog_instance* inst, bool compile_jit) {
         rc = build_decomposition(inst->n_vars, inst->cost.data(), inst->n_rows, inst->row_ptr.data(),
                                  inst->col.data(), inst->coef.data(), inst->sense.data(), inst->rhs.data(),
                                  inst->jit_failed ? -1 : inst->params.jit, inst->params.fuse >= 0, inst->dec,
-                                 inst->last_error);
+                                 inst->last_error, inst->shard ? inst->shard_shared.data() : nullptr);
     } catch (const std::bad_alloc&) {
         rc = FDOG_ENOMEM;
     } catch (...) {
         rc = FDOG_EINVAL;
     }
     if (rc != FDOG_OK) return rc;
+    if (inst->shard && (rc = shard_check_copies(inst)) != FDOG_OK) return rc;
     inst->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     inst->planned_on_device = false;
     if ((rc = check_layer_limits(inst)) != FDOG_OK) return rc;
@@ -157,7 +161,7 @@ int plan(fdog_instance* inst, bool compile_jit) {
 static int plan_for_build(fdog_instance* inst) {
     if (inst->planned) return FDOG_OK;
     const int mode = inst->params.planner;
-    if (mode != 1 && inst->params.update == 0) {
+    if (mode != 1 && inst->params.update == 0 && !inst->shard) {
         int rc = plan_on_device(inst, inst->jit_failed ? -1 : inst->params.jit, inst->params.fuse >= 0);
         if (rc == FDOG_OK) {
             if ((rc = check_layer_limits(inst)) != FDOG_OK) {
@@ -180,7 +184,7 @@ static int plan_for_build(fdog_instance* inst) {
     }
     if (mode == 2) {
         inst->last_error = "the device planner does not take this instance (presolve work, serial update, "
-                           "too many row signatures or copies)";
+                           "a shard of a split instance, too many row signatures or copies)";
         return FDOG_EUNSUPPORTED;
     }
     return plan(inst);
@@ -380,6 +384,20 @@ int allocate_and_upload(fdog_instance* inst) {
     up(a.lev_f, d.lev_f_vars.data(), sizeof(int32_t) * d.lev_f_vars.size());
     up(a.lev_b, d.lev_b_vars.data(), sizeof(int32_t) * d.lev_b_vars.size());
     up(a.prefix, pre.data(), sizeof(int32_t) * kPrefixInts);
+    if (!d.shared_vars.empty()) {
+        // copy counts over all shards, and each variable's rank among all shared variables
+        std::vector<int32_t> cnt(d.shared_vars.size()), slot(d.shared_vars.size());
+        std::vector<int32_t> rank(static_cast<size_t>(n) + 1, 0);
+        for (int64_t i = 0; i < n; ++i) rank[i + 1] = rank[i] + inst->shard_shared[i];
+        for (size_t k = 0; k < cnt.size(); ++k) {
+            cnt[k] = inst->shard_copies[d.shared_vars[k]];
+            slot[k] = rank[d.shared_vars[k]];
+        }
+        // pageable sources: staged before each call returns
+        up(a.sh_vars, d.shared_vars.data(), sizeof(int32_t) * d.shared_vars.size());
+        up(a.sh_copies, cnt.data(), sizeof(int32_t) * cnt.size());
+        up(a.sh_slot, slot.data(), sizeof(int32_t) * slot.size());
+    }
     if (e != cudaSuccess) return fail_cuda(inst, e, "upload");
     return FDOG_OK;
 }
@@ -447,11 +465,12 @@ int reset_dual_state(fdog_instance* inst) {
     c.window = p.window;
     c.min_iters = p.min_iters;
     c.tol = p.tol;
-    c.iter_limit = 0;
+    c.iter_limit = inst->shard ? INT32_MAX : 0;  // a shard's passes are driven by fdog_shard_pass
     c.delta = p.delta;
     cudaError_t e = copy_async(inst, inst->dev.ctl, &c, sizeof(c), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail_cuda(inst, e, "reset ctl");
     e = launch_init(inst->batch, inst->cfg, inst->stream);
+    if (e == cudaSuccess && inst->shard) e = launch_shard_init(inst);
     if (e != cudaSuccess) return fail_cuda(inst, e, "init");
     inst->pending_T = false;
     inst->iterated = false;
@@ -858,6 +877,10 @@ int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* swee
 int fdog_dual_iterate(fdog_instance* inst, int32_t k, int32_t* iters_done, double* lb) {
     if (!inst || k < 0) return FDOG_EINVAL;
     if (!inst->built) return FDOG_ESTATE;
+    if (inst->shard) {
+        inst->last_error = "a shard of a split instance iterates through fdog_shard_pass";
+        return FDOG_ESTATE;
+    }
     DeviceGuard g(inst->device);
     InstCtl before;
     int rc = read_ctl(inst, before);
@@ -996,6 +1019,10 @@ int fdog_multipliers(fdog_instance* inst, int64_t* n_slots, int32_t* var, int32_
 int fdog_primal_round(fdog_instance* inst, int32_t* rounds_used) {
     if (!inst) return FDOG_EINVAL;
     if (!inst->built) return FDOG_ESTATE;
+    if (inst->shard) {
+        inst->last_error = "rounding a split instance needs every shard's min-marginals";
+        return FDOG_EUNSUPPORTED;
+    }
     DeviceGuard g(inst->device);
     Engine* e;
     BatchView* v;

@@ -32,6 +32,7 @@ int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream,
         for (int32_t j = 0; j < i; ++j)
             if (insts[j] == insts[i]) return FDOG_EINVAL;  // an instance may appear once
         if (n > 1 && insts[i]->params.update == 1) return FDOG_EUNSUPPORTED;  // the serial update runs alone
+        if (insts[i]->shard) return FDOG_EUNSUPPORTED;  // a shard's passes wait on the other shards
     }
     fdog_batch* b = new (std::nothrow) fdog_batch();
     if (!b) return FDOG_ENOMEM;

@@ -295,7 +295,8 @@ void build_templates(Decomposition& out) {
 
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err) {
+                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err,
+                        const uint8_t* shared) {
     out = Decomposition();
     out.fixed.assign(n_vars, -1);
 
@@ -380,6 +381,18 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
                 ++t;
             }
         }
+    }
+
+    if (shared) {
+        // a shard of a split instance: presolve would fix variables that other
+        // shards' rows also hold, so a shard must not need it
+        for (int32_t j = 0; j < n_rows; ++j)
+            if (!alive[j]) { err = "shard row " + std::to_string(j) + " needs presolve"; return FDOG_EUNSUPPORTED; }
+        for (int32_t i = 0; i < n_vars; ++i)
+            if (out.fixed[i] == 0 || out.fixed[i] == 1) {
+                err = "shard presolve fixes variable " + std::to_string(i);
+                return FDOG_EUNSUPPORTED;
+            }
     }
 
     // surviving rows: their analysis holds the final shape
@@ -528,7 +541,7 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
             int64_t m = 0;
             for (int64_t p = lo; p < hi; ++p) {
                 const int32_t v = out.var[p];
-                if (v < 0) continue;
+                if (v < 0 || (shared && shared[v])) continue;  // a shared variable's sum spans shards
                 const int32_t b = out.csr_off[v], c = out.csr_off[v + 1] - b;
                 if (c > 4 || out.csr_pos[b] != p || out.csr_pos[b + c - 1] >= hi) continue;  // p is the first copy
                 if (dst) {
@@ -578,6 +591,8 @@ int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, cons
         const int32_t c = out.csr_off[i + 1] - out.csr_off[i];
         if (local[i]) {
             ++out.n_local_vars;
+        } else if (shared && shared[i]) {
+            if (c > 0) out.shared_vars.push_back(i);  // deferred term from the sum over all shards
         } else if (c > 0) {
             bucket[std::min(c, FDOG_WBUCKETS) - 1].push_back(i);
             out.n_work_slots += c;

@@ -205,6 +205,7 @@ struct Decomposition {
     std::vector<uint16_t> local_ent;
     std::vector<int32_t> work;      // variables left to the deferred-sum kernel, bucketed by copy count
     std::vector<int32_t> wpos;      // bucketed slot positions (see InstDev::wpos)
+    std::vector<int32_t> shared_vars;  // shard of a split instance: variables with copies in other shards
     // serial schedule (update = 1, Eq. 4); empty otherwise
     std::vector<int32_t> tile_of_row;          // tile of each row of 32 padded slots
     std::vector<int32_t> lab_off;              // per tile: first float of its label region
@@ -287,10 +288,15 @@ inline void parallel_chunks(int64_t n, F&& fn) {
 // Builds the decomposition: presolve, BDDs per row (shared per row
 // signature), tiles, interleaved slots and the per-variable slot lists.
 // jit_mode: -1 no shape-specialised class; 0 eligible shapes with at least
-// kJitMinBdds BDDs; 1 every eligible shape.  Returns an FDOG_* status.
+// kJitMinBdds BDDs; 1 every eligible shape.  shared (n_vars flags, may be
+// null): the instance is one shard of a split instance and these variables
+// also have copies in other shards; they are kept out of the tile-local and
+// deferred-sum lists and listed in shared_vars, and a shard whose rows would
+// need presolve is refused (FDOG_EUNSUPPORTED).  Returns an FDOG_* status.
 int build_decomposition(int32_t n_vars, const double* cost, int32_t n_rows, const int64_t* row_ptr,
                         const int32_t* col, const int32_t* coef, const int8_t* sense, const int64_t* rhs,
-                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err);
+                        int jit_mode, bool fuse_local, Decomposition& out, std::string& err,
+                        const uint8_t* shared = nullptr);
 
 // The schedule of the serial update (Eq. 4) on a built decomposition: a
 // variable's ascending level is one more than the largest level of the

@@ -52,6 +52,9 @@ struct DevArrays {
     double* chunk_lb = nullptr;
     double* obj_chunk = nullptr;
     int32_t* prefix = nullptr;
+    int32_t* sh_vars = nullptr;      // shard of a split instance: its shared variables (ascending)
+    int32_t* sh_copies = nullptr;    // and their copy counts over all shards
+    int32_t* sh_slot = nullptr;      // and their index among all shared variables (the exchange buffer)
 };
 
 }  // namespace fdog
@@ -90,6 +93,12 @@ struct fdog_instance {
     bool jit_failed = false;  // NVRTC unavailable or failed: generic kernels only
     std::string jit_note;
 
+    // shard of a split instance (fdog_shard_setup): which variables also have
+    // copies in other shards, and every variable's copy count over all shards
+    bool shard = false;
+    std::vector<uint8_t> shard_shared;
+    std::vector<int32_t> shard_copies;
+
     // host-side view of the dual state
     bool pending_T = false;  // deferred differences of the last pass not yet added back
     bool iterated = false;   // iterations ran since the last add-back (running bound available)
@@ -126,4 +135,8 @@ int fail_cuda(fdog_instance* inst, cudaError_t e, const char* where);
 cudaError_t copy_async(fdog_instance* inst, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind);
 int read_ctl(fdog_instance* inst, InstCtl& out);
 int addback(fdog_instance* inst);
+// shards of a split instance (shard.cu): the copy counts given at set-up
+// against the plan, and the initial multipliers of the shared variables
+int shard_check_copies(fdog_instance* inst);
+cudaError_t launch_shard_init(fdog_instance* inst);
 }  // namespace fdog

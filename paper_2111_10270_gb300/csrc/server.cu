@@ -224,6 +224,10 @@ int fdog_server_submit(fdog_server* s, fdog_instance* inst, uint64_t* ticket) {
         inst->last_error = "an instance with the serial update (update = 1) runs alone";
         return FDOG_EUNSUPPORTED;
     }
+    if (inst->shard) {
+        inst->last_error = "a shard of a split instance runs through fdog_shard_pass";
+        return FDOG_EUNSUPPORTED;
+    }
     // host work in the caller's thread: planning and the specialised kernels
     int rc = plan(inst, false);
     if (rc != FDOG_OK) return rc;

@@ -40,9 +40,15 @@ WORKLOADS = {
     # small case (the parity-test size)
     "mrf8": dict(h=8, w=8, labels=3, seed=0, potts_max=1.0, max_iters=200,
                  desc="MRF grid 8x8, 3 labels, Potts U(0,1), unary N(0,1), seed 0"),
-    # QAP-shaped graph matching: 500 x 1000 nodes, 20 candidates, 10-NN product terms with AND rows
-    "qap500": dict(kind="qap", left=500, right=1000, cand=20, knn=10, seed=2, max_iters=500,
-                   desc="QAP-shaped matching 500x1000, 20 candidates, 10-NN AND products, costs N(0,1), seed 2"),
+    # QAP-shaped graph matching: 500 x 1000 nodes, 20 candidates, product terms (AND rows) between matches
+    # whose left nodes and right nodes are 10-NN neighbours
+    "qap500": dict(kind="qap", left=500, right=1000, cand=20, knn=10, seed=2, max_iters=500, sparse=True,
+                   desc="QAP-shaped matching 500x1000, 20 candidates, AND products of 10-NN neighbour matches "
+                        "(both sides), costs N(0,1), seed 2"),
+    # the denser reading: products for every candidate pair of 10-NN left nodes (1.17M variables)
+    "qap500_dense": dict(kind="qap", left=500, right=1000, cand=20, knn=10, seed=2, max_iters=500, sparse=False,
+                         desc="QAP-shaped matching 500x1000, 20 candidates, AND products of every candidate pair of "
+                              "10-NN left nodes, costs N(0,1), seed 2"),
     # one instance of the cell-tracking batch (its first child seed)
     "cell1": dict(kind="cell", seed=3, max_iters=500,
                   desc="cell-tracking instance (first of the seed-3 batch): frames U{10..80}, "
@@ -69,11 +75,13 @@ def parse():
     ap.add_argument("--dual-only", action="store_true", help="steps without rounding (profiling runs)")
     ap.add_argument("--batch-instances", type=int, default=64,
                     help="cell-tracking batch size for the batched-vs-sequential section (0: skip)")
-    ap.add_argument("--serve-instances", type=int, default=48,
+    ap.add_argument("--serve-instances", type=int, default=200,
                     help="requests of the serving stream replayed in the serving section (0: skip)")
     ap.add_argument("--schemes", type=int, default=1, help="update-scheme comparison section (0: skip)")
     ap.add_argument("--split", type=int, default=1, help="long-row splitting section (0: skip)")
     ap.add_argument("--lb-star", type=int, default=1, help="time to 1e-4 of the stored FP64 LB* (mrf512; 0: skip)")
+    ap.add_argument("--per-workload", type=int, default=1,
+                    help="dual throughput and roofline of the QAP and cell-tracking workloads (0: skip)")
     ap.add_argument("--threads", type=int, default=min(16, os.cpu_count() or 1),
                     help="host threads / processes for instance generation and planning")
     return ap.parse_args()
@@ -103,7 +111,7 @@ def make_workload(name):
 
     w = WORKLOADS[name]
     if w.get("kind") == "qap":
-        return ilpgen.qap(w["seed"], w["left"], w["right"], w["cand"], w["knn"]), w
+        return ilpgen.qap(w["seed"], w["left"], w["right"], w["cand"], w["knn"], sparse=w["sparse"]), w
     if w.get("kind") == "cell":
         return ilpgen.cell_tracking(ilpgen._child_seeds(w["seed"], 1)[0]), w
     return ilpgen.mrf_grid(w["h"], w["w"], w["labels"], w["seed"], potts_max=w["potts_max"]), w
@@ -240,21 +248,6 @@ def generate(fn, args, threads):
         return list(ex.map(fn, args))
 
 
-def plan_all(P, ilps, params, threads):
-    """Instances planned on the host in parallel (the C planner releases the
-    GIL); returns them with each one's planning seconds."""
-    from concurrent.futures import ThreadPoolExecutor
-
-    def one(g):
-        t0 = time.perf_counter()
-        inst = P.Instance.from_ilp(g, params)
-        inst.plan()
-        return inst, time.perf_counter() - t0
-
-    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
-        return list(ex.map(one, ilps))
-
-
 def pct(v, q):
     return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
 
@@ -308,6 +301,8 @@ def batched_section(torch, P, dev, stream, params, n_inst, threads):
     same = all(seq[q][0] == iters[q] and seq[q][1] == rounds[q] and seq[q][2] == status[q]
                and np.array_equal(seq[q][3], sols[q][0]) and seq[q][4] == sols[q][1] for q in range(n_inst))
     feasible = sum(1 for q in range(n_inst) if sols[q][2])
+    kr = params.rounding_dual_iters
+    arcs = sum(4.0 * insts[q].info()["n_nodes"] * (int(iters[q]) + int(rounds[q]) * kr) for q in range(n_inst))
     batch.close()
     for i in insts:
         i.close()
@@ -318,6 +313,9 @@ def batched_section(torch, P, dev, stream, params, n_inst, threads):
         "batched_instances_per_s": n_inst / t_bat, "sequential_instances_per_s": n_inst / t_seq,
         "speedup": t_seq / t_bat, "batched_s": t_bat, "sequential_s": t_seq,
         "results_identical": bool(same), "feasible": feasible,
+        "rounding_noconverge": int(sum(1 for st in status if st == P.FDOG_ENOCONVERGE)),
+        "rounds_p50": pct([int(r) for r in rounds], 50), "rounds_max": int(max(rounds)),
+        "batched_arc_updates_per_s": arcs / t_bat, "sequential_arc_updates_per_s": arcs / t_seq,
         "dual_iters_p50": pct([r[0] for r in seq], 50), "dual_iters_max": max(r[0] for r in seq),
         "plan_s_p50": pct([t for _, t in plan_stats], 50),
         "planned_on_device": sum(1 for od, _ in plan_stats if od),
@@ -326,9 +324,12 @@ def batched_section(torch, P, dev, stream, params, n_inst, threads):
 
 def serving_section(torch, P, dev, stream, params, n_req, threads):
     """Replays the first n_req requests of the seeded Poisson stream (200/s;
-    MRF and QAP mix) twice on planned instances: through the continuous-
-    batching server, and one at a time in arrival order (upload, solve, read
-    back, free).  Latency = result time - arrival time."""
+    MRF and QAP mix) twice: through the continuous-batching server, and one at
+    a time in arrival order.  Each request is created from its host arrays at
+    its arrival time and submitted unplanned: the server builds its
+    decomposition on the device when it admits it; one at a time, each
+    request is built (same device builder), solved, read back and freed.
+    Latency = result time - arrival time, so planning is inside it."""
     import ilpgen
 
     specs = ilpgen.serving_stream(4)[:n_req]
@@ -336,64 +337,63 @@ def serving_section(torch, P, dev, stream, params, n_req, threads):
     arrivals = np.array([sp["arrival"] for sp in specs]) - specs[0]["arrival"]
     max_iters = 500
     free, _ = torch.cuda.mem_get_info(dev)
-    # every request that fits is admitted (throughput; a budget just large enough
-    # to saturate the GPU lowers the median latency at some cost in instances/s)
-    budget = int(free * 0.8)
+    budget = int(free * 0.8)  # every request that fits is admitted
 
-    # planned once; a retired instance keeps its plan and can be served or built again
-    planned = plan_all(P, ilps, params, threads)
-    insts = [inst for inst, _ in planned]
-    plan_s = [t for _, t in planned]
-
-    def run_server(budget):
+    def run_server():
         srv = P.Server(dev, hbm_budget=budget, max_active=256, max_iters=max_iters)
         l0 = srv.stats()["kernel_launches"]
         t0 = time.perf_counter()
-        tickets = []
-        for q, inst in enumerate(insts):
+        tickets, delay = [], []
+        for q, g in enumerate(ilps):
             d = t0 + arrivals[q] - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            tickets.append(srv.submit(inst))
+            tickets.append(srv.submit(P.Instance.from_ilp(g, params)))
+            delay.append(time.perf_counter() - (t0 + arrivals[q]))  # creation and submission after arrival
         for t in tickets:
-            if not srv.wait(t, 600.0):
+            if not srv.wait(t, 1200.0):
                 raise RuntimeError("server request timed out")
-        lat = [srv.poll(t)["latency_s"] for t in tickets]
         t_end = time.perf_counter()
-        res = [srv.take(t).solution() for t in tickets]
+        polls = [srv.poll(t) for t in tickets]
+        lat = [delay[q] + polls[q]["latency_s"] for q in range(len(tickets))]
+        res, on_dev = [], 0
+        for t in tickets:
+            inst = srv.take(t)
+            res.append(inst.solution())
+            on_dev += inst.plan_stats()[0]
+            inst.close()
         launches = srv.stats()["kernel_launches"] - l0
         srv.close()
-        return lat, t_end - t0, res, launches
+        return lat, t_end - t0, res, [p["status"] for p in polls], launches, on_dev
 
     def run_sequential():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        lat, res = [], []
-        for q, inst in enumerate(insts):
+        lat, res, status = [], [], []
+        for q, g in enumerate(ilps):
             d = t0 + arrivals[q] - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-            inst.build(dev, stream)
+            inst = P.Instance.from_ilp(g, params).build(dev, stream)
             inst.iterate(max_iters)
-            inst.primal_round()
+            rc, _ = inst.primal_round()
             res.append(inst.solution())
-            inst.release()
+            status.append(rc)
+            inst.close()
             lat.append(time.perf_counter() - (t0 + arrivals[q]))
-        return lat, time.perf_counter() - t0, res
+        return lat, time.perf_counter() - t0, res, status
 
-    run_server(budget)  # warm-up: specialised modules of the growing shape universe, graphs
-    lat_srv, t_srv, res_srv, launches = run_server(budget)
-    # latency mode: admit only about enough resident work to saturate the GPU
-    budget_lat = int(min(budget, 3e9))
-    lat_srv2, t_srv2, _, _ = run_server(budget_lat)
-    lat_seq, t_seq, res_seq = run_sequential()
-    for inst in insts:
-        inst.close()
+    run_server()  # warm-up: specialised modules of the growing shape set, graphs
+    lat_srv, t_srv, res_srv, st_srv, launches, on_dev = run_server()
+    lat_seq, t_seq, res_seq, st_seq = run_sequential()
     same = all(np.array_equal(a[0], b[0]) and a[1] == b[1] for a, b in zip(res_srv, res_seq))
+    same = same and st_srv == st_seq
     n_vars = sum(g.n_vars for g in ilps)
+    kinds = [sp["kind"] for sp in specs]
     return {
         "workload": f"serving stream: first {n_req} of 10,000 seeded requests, Poisson 200/s, 50% MRF "
-                    f"(side U{{16..256}}, labels U{{2..8}}), 50% QAP (left U{{50..1000}}), seed 4; "
+                    f"(side U{{16..256}}, labels U{{2..8}}), 50% QAP (left U{{50..1000}}, products of 10-NN "
+                    f"neighbour matches), seed 4; {kinds.count('mrf')} MRF, {kinds.count('qap')} QAP, "
                     f"{n_vars} variables in all",
         "metric": "instances/s and latency from arrival to result (1e-4 LB-gap stopping rule + rounding)",
         "server_instances_per_s": n_req / t_srv, "sequential_instances_per_s": n_req / t_seq,
@@ -401,12 +401,13 @@ def serving_section(torch, P, dev, stream, params, n_req, threads):
         "server_latency_p50_s": pct(lat_srv, 50), "server_latency_p99_s": pct(lat_srv, 99),
         "sequential_latency_p50_s": pct(lat_seq, 50), "sequential_latency_p99_s": pct(lat_seq, 99),
         "results_identical": bool(same), "server_kernel_launches": launches,
-        "host_plan_s_p50": pct(plan_s, 50), "host_plan_s_p99": pct(plan_s, 99),
-        "scope": "requests arrive planned (host BDD construction timed separately as host_plan_s); "
-                 "upload, solve and read-back inside the latency",
+        "rounding_noconverge": int(sum(1 for v in st_srv if v == P.FDOG_ENOCONVERGE)),
+        "failed": int(sum(1 for v in st_srv if v not in (P.FDOG_OK, P.FDOG_ENOCONVERGE))),
+        "feasible": int(sum(1 for r in res_srv if r[2])),
+        "planned_on_device": int(on_dev),
+        "scope": "requests created from host arrays at arrival and submitted unplanned: BDD construction on "
+                 "the device, upload, solve and read-back inside the latency",
         "server_admission_budget_bytes": budget,
-        "latency_mode": {"admission_budget_bytes": budget_lat, "server_instances_per_s": n_req / t_srv2,
-                         "server_latency_p50_s": pct(lat_srv2, 50), "server_latency_p99_s": pct(lat_srv2, 99)},
     }
 
 
@@ -494,6 +495,72 @@ def split_section(torch, P, dev, stream):
                       "bound_at_stop": float(lb_stop), "seconds_to_stop": t_stop, "bound_after_1500": float(lb_fixed),
                       "ms_per_iter": ms_iter, "generic_kernel_tiles": int(seg_tiles)}
     return {"instance": "QAP-shaped matching 500x1000, 20 candidates, 10-NN AND products, seed 2", "cases": cases}
+
+
+def iteration_bytes(kp, info):
+    """Compulsory bytes of one dual iteration (two update sweeps, two
+    deferred-sum passes): every array element counted once per launch (see
+    the roofline block of main)."""
+    tiles = kp["jit_tiles"] + kp["static_tiles"]
+    sweep = 12 * info["n_slots"] + 4 * (kp["local_vars"] + kp["work_vars"]) + 40 * tiles + 8 * kp["local_vars"]
+    reduce = 12 * kp["work_vars"] + 8 * kp["work_slots"]
+    return sweep, reduce, 2 * (sweep + reduce)
+
+
+def per_workload_section(torch, P, dev, stream, peak):
+    """Dual-iteration throughput of the QAP-shaped matching and one
+    cell-tracking instance solved alone: BDD arc-updates/s and device time per
+    iteration over a fixed number of iterations (no early stop, iteration
+    graphs on), then the same iterations with per-launch CUDA events for the
+    dominant update sweep and the deferred-sum step; their compulsory bytes
+    over those times, as fractions of the measured HBM bandwidth; and the
+    full solve's rounding outcome (Alg. 2)."""
+    import ilpgen
+
+    out = {}
+    for name in ("qap500", "qap500_dense", "cell1"):
+        g, w = make_workload(name)
+        iters = 200
+        inst = P.Instance.from_ilp(g, tol=0.0).build(dev, stream)
+        info, kp = inst.info(), inst.kernel_plan()
+        inst.iterate(20)  # warm-up: graphs, modules
+        inst.reset()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        inst.iterate(iters)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_iter = ev0.elapsed_time(ev1) / 1e3 / iters
+        inst.reset()
+        inst.profile_read()
+        inst.set_profiling(True)
+        inst.iterate(iters)
+        inst.set_profiling(False)
+        prof = inst.profile_read()
+        sweep_b, reduce_b, iter_b = iteration_bytes(kp, info)
+        sw = prof["sweep_ms"] / max(prof["sweep_launches"], 1) / 1e3
+        rd = prof["reduce_ms"] / max(prof["reduce_launches"], 1) / 1e3
+        inst.close()
+        # the full solve (stopping rule + rounding) of the same instance
+        full = P.Instance.from_ilp(g, P.capi.default_params(tol=1e-4)).build(dev, stream)
+        r = solve(full, w["max_iters"], full.params.rounding_dual_iters)
+        full.close()
+        out[name] = {
+            "workload": w["desc"], "vars": info["n_vars"], "bdds": info["n_bdds"], "slots": info["n_slots"],
+            "nodes": info["n_nodes"], "arc_updates_per_s": 4.0 * info["n_nodes"] / t_iter,
+            "ms_per_iter": t_iter * 1e3, "iteration_bytes": iter_b,
+            "iteration_gbs": iter_b / t_iter / 1e9, "iteration_frac": iter_b / t_iter / 1e9 / peak,
+            "sweep": {"avg_launch_us": sw * 1e6, "alg_bytes_per_launch": sweep_b,
+                      "achieved_gbs": sweep_b / sw / 1e9 if sw else None,
+                      "frac": sweep_b / sw / 1e9 / peak if sw else None},
+            "deferred_sums": {"avg_launch_us": rd * 1e6, "alg_bytes_per_launch": reduce_b,
+                              "achieved_gbs": reduce_b / rd / 1e9 if rd else None,
+                              "frac": reduce_b / rd / 1e9 / peak if rd else None},
+            "full_solve": {"dual_iters": r["iters"], "rounds": r["rounds"], "status": r["rc"],
+                           "feasible": r["feasible"], "lb": r["lb"], "ub": r["obj"]},
+        }
+    return out
 
 
 LB_STAR_FILE = os.path.join(ROOT, "tests", "golden", "mrf512_lb_star.txt")
@@ -691,12 +758,14 @@ def main():
                          f"(FP64 single-threaded C oracle; its BDD construction not timed)"}
 
     # ---- batched and served instance mixes (rank 0, N = 1) ---------------------
-    batched = served = schemes = split = lb_star = None
+    batched = served = schemes = split = lb_star = per_workload = None
     if rank == 0 and world == 1 and args.lb_star and args.workload == "mrf512":
         try:
             lb_star = lb_star_section(torch, P, g, dev, stream)
         except Exception as exc:  # a report section: its failure must not cost the bench line
             lb_star = {"error": f"{type(exc).__name__}: {exc}"}
+    if rank == 0 and world == 1 and args.per_workload:
+        per_workload = per_workload_section(torch, P, dev, stream, peak)
     if rank == 0 and world == 1 and args.schemes:
         schemes = update_scheme_section(P, dev, stream)
     if rank == 0 and world == 1 and args.split:
@@ -714,13 +783,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["desc"], "vars": info["n_vars"], "bdds": n_bdds, "slots": S, "nodes": nodes,
                        "dual_iters_per_step": dual_iters / args.steps, "stop_iters": last["iters"],
-                       "rounds": last["rounds"], "lb": last["lb"], "ub": last["obj"], "feasible": last["feasible"],
+                       "rounds": last["rounds"], "rounding_status": last["rc"], "lb": last["lb"], "ub": last["obj"],
+                       "feasible": last["feasible"],
                        "l2": (f"inputs larger than L2 ({dev_bytes / 1e6:.0f} MB resident, L2 129 MB)" if dev_bytes > 129e6
                               else f"inputs fit in L2 ({dev_bytes / 1e6:.0f} MB resident); no flush between steps"),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-            "batched": batched, "serving": served, "update_schemes": schemes, "long_rows": split,
-            "time_to_lb_star": lb_star,
+            "per_workload": per_workload, "batched": batched, "serving": served, "update_schemes": schemes,
+            "long_rows": split, "time_to_lb_star": lb_star,
         }
         print(json.dumps(line), flush=True)
     inst.close()

@@ -377,9 +377,10 @@ def cell_tracking_batch(seed: int = 3, n: int = 64, **kw) -> list[ILP]:
 def serving_stream(seed: int = 4, n: int = 10000, rate: float = 200.0) -> list[dict]:
     """Specs of a seeded request stream: Poisson arrivals at `rate` per second;
     half MRF grids (side ~ U{16..256}, labels ~ U{2..8}, Potts U(0,1)), half
-    QAP (left ~ U{50..1000}, right = 2 left, candidates min(20, right)).  Each
-    spec holds its arrival time and the arguments of its generator; build the
-    instance with stream_instance(spec)."""
+    QAP (left ~ U{50..1000}, right = 2 left, candidates min(20, right), product
+    terms between 10-NN neighbour matches on both sides: qap(..., sparse=True)).
+    Each spec holds its arrival time and the arguments of its generator; build
+    the instance with stream_instance(spec)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, n))
     kinds = rng.random(n) < 0.5
@@ -401,4 +402,4 @@ def stream_instance(spec: dict) -> ILP:
     if spec["kind"] == "mrf":
         return mrf_grid(spec["side"], spec["side"], spec["labels"], spec["seed"], potts_max=1.0)
     nl = spec["left"]
-    return qap(spec["seed"], nl, 2 * nl, min(20, 2 * nl))
+    return qap(spec["seed"], nl, 2 * nl, min(20, 2 * nl), sparse=True)

@@ -418,17 +418,23 @@ void fdog_batch_destroy(fdog_batch* batch);
  * together: each scheduling step runs a chunk of dual iterations for the
  * instances still iterating and the rounding tests / perturbations of the
  * others, so requests that arrive while others are on the GPU join the
- * running set as soon as a slot (max_active) and HBM (hbm_budget bytes, from
- * each instance's planned size) are free, in arrival order.  An instance is
+ * running set as soon as a slot (max_active) and HBM (hbm_budget bytes) are
+ * free, in arrival order.  An instance is
  * retired when its stopping rule (tol, window, min_iters, or max_iters
  * iterations) has fired and rounding has agreed (or hit max_rounds); its
  * device memory is then freed and its solution kept on the host.  Results
  * equal those of solving each instance alone.
  *
- * fdog_server_submit: `inst` must be created and not built; the call plans it
- * in the caller's thread (host work, errors returned here) and queues it;
- * ownership moves to the server until fdog_server_take.  *ticket identifies
- * the request.
+ * fdog_server_submit: `inst` must be created and not built; ownership moves
+ * to the server until fdog_server_take.  *ticket identifies the request.  An
+ * unplanned instance is only queued, with an upper bound of the device
+ * memory it may need (from its sizes); at admission the worker builds its
+ * decomposition on the device (the host builder for instances the device
+ * builder does not take, see params.planner) and the reservation becomes
+ * the memory the instance holds.  Planning errors then arrive as the
+ * request's status (fdog_server_poll).  An instance already planned
+ * (fdog_plan) or with planner = 1 is planned here, in the caller's thread,
+ * and its errors are returned here.
  * fdog_server_poll: *state 0 queued, 1 resident, 2 done; *status FDOG_OK /
  * FDOG_ENOCONVERGE / error of the request; *lb the running bound at
  * retirement; *latency_s submit-to-done time (or time so far).

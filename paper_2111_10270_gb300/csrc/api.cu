@@ -103,6 +103,26 @@ size_t arena_size(const fdog_instance* inst) {
     return total;
 }
 
+// Upper bound of the device memory fdog_build_bdds needs for an unplanned
+// instance that the device builder plans: the builder's temporaries (the
+// uploaded rows, hash tables, keys and ranks) plus the instance's arena,
+// bounded from the ILP's sizes alone (at most 1,024 shapes, each padding its
+// last tile by at most 31 BDDs; at most 16 nodes per layer).
+int64_t device_plan_bytes_bound(const fdog_instance* inst) {
+    const int64_t n = inst->n_vars, m = inst->n_rows, nnz = inst->row_ptr[m];
+    int64_t maxk = 0;
+    for (int64_t j = 0; j < m; ++j) maxk = std::max<int64_t>(maxk, inst->row_ptr[j + 1] - inst->row_ptr[j]);
+    const int64_t shapes = std::min<int64_t>(m, 1024);
+    const int64_t nt = (m + kTile - 1) / kTile + shapes;
+    const int64_t S = nnz + std::min<int64_t>(31 * shapes * maxk, 31 * nnz);
+    const int64_t tpl = 2 * 16 * std::min<int64_t>(nnz, shapes * maxk);
+    const int64_t arena = static_cast<int64_t>(sizeof(InstDev) + sizeof(InstCtl)) + 48 * nt + 16 * shapes + tpl +
+                          12 * S + 29 * n + 4 + 8 * nnz + 8 * nt + 4 * (nt / kLbChunk + 1) * 2 +
+                          8 * (n / kObjChunk + 1) + 4 * kPrefixInts + 40 * 256;
+    const int64_t temporaries = 48 * nnz + 64 * m + (64 << 20);
+    return arena + temporaries;
+}
+
 std::vector<int> jit_ids(const fdog_instance* inst) {
     std::vector<int> ids;
     for (const ShapeDev& s : inst->dec.shape_dev)

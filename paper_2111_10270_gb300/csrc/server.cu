@@ -1,13 +1,16 @@
 // Continuous-batching server (fdog_server_*).
 //
-// Callers submit instances at any time.  The submitting thread plans them
-// (presolve, BDDs, layout, shape-specialised kernels: host work only) and
-// queues them.  One worker thread owns a private stream and an engine: it
-// admits queued instances in arrival order while the HBM they need fits the
-// budget and a slot is free, uploads them, and then advances every resident
-// instance together, one scheduling step at a time (a chunk of dual
-// iterations for the iterating ones, rounding tests and perturbations for the
-// others).  An instance that finishes -- stopping rule met and rounding
+// Callers submit instances at any time; submission only queues them, with
+// an upper bound of the device memory each needs, from the ILP's sizes.  One
+// worker thread owns a private stream and an engine: it admits queued
+// instances in arrival order while that memory fits the budget and a slot is
+// free, builds each admitted one's decomposition on the device (BDDs, layout,
+// slot lists; the host builder only for instances the device builder does not
+// take) and corrects its memory to the arena it holds, and then advances
+// every resident instance together, one scheduling step at a time (a chunk of
+// dual iterations for the iterating ones, rounding tests and perturbations
+// for the others).  Instances submitted already planned (fdog_plan, or
+// params.planner = 1) keep their host plan.  An instance that finishes -- stopping rule met and rounding
 // agreed -- is retired at once: its solution is kept on the host, its device
 // memory freed for the next admission.  Each result is the one the instance
 // would get alone (engine_step runs the same per-instance schedule).
@@ -36,7 +39,8 @@ double now_s() {
 struct Job {
     uint64_t ticket = 0;
     fdog_instance* inst = nullptr;
-    int64_t bytes = 0;
+    int64_t bytes = 0;         // device memory accounted to the job (a bound until it is built)
+    bool plan_on_admit = false;  // the worker plans it at admission
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     int state = 0;  // 0 queued, 1 resident, 2 done (see status), 3 taken
     int status = FDOG_OK;
@@ -76,6 +80,7 @@ using namespace fdog;
 namespace fdog {
 int plan(fdog_instance* inst, bool compile_jit);
 size_t arena_size(const fdog_instance* inst);
+int64_t device_plan_bytes_bound(const fdog_instance* inst);
 std::vector<int> jit_ids(const fdog_instance* inst);
 int release_device(fdog_instance* inst);
 int build_instance(fdog_instance* inst, int32_t device, void* cuda_stream, bool autotune);
@@ -112,14 +117,40 @@ void worker_main(fdog_server* s) {
         const double t0 = now_s();
         const size_t first = s->active.size();
         for (Job* j : admit) {
-            int rc = build_instance(j->inst, s->device, s->stream, false);  // the server's engine sets launch shapes
+            // plans an unplanned instance on the server's stream, then uploads it; the server's
+            // engine sets the launch shapes
+            int rc = build_instance(j->inst, s->device, s->stream, false);
+            std::vector<int> grown;
+            if (rc == FDOG_OK && j->plan_on_admit) {
+                // its shapes join the set the engine's specialised module covers
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (int id : jit_ids(j->inst))
+                    if (std::find(s->jit_universe.begin(), s->jit_universe.end(), id) == s->jit_universe.end()) {
+                        s->jit_universe.push_back(id);
+                        grown.push_back(id);
+                    }
+                if (!grown.empty()) grown = s->jit_universe;
+            }
+            if (!grown.empty()) {
+                std::string why;
+                rc = jit_compile(grown, why);  // cached per shape set: only new sets compile
+                if (rc != FDOG_OK) j->inst->last_error = why;
+            }
             std::lock_guard<std::mutex> lk(s->mu);
             if (rc != FDOG_OK) {
                 s->used -= j->bytes;
                 fail_job(s, j, rc);
+                if (j->inst->built) release_device(j->inst);
                 s->cv_done.notify_all();
                 continue;
             }
+            if (j->plan_on_admit) {
+                // the bound accounted at admission becomes the arena the instance holds
+                const int64_t exact = static_cast<int64_t>(j->inst->arena_bytes);
+                s->used += exact - j->bytes;
+                j->bytes = exact;
+            }
+            s->engine.jit_universe = s->jit_universe;
             j->t_admit = now_s();
             j->state = 1;
             Member m;
@@ -228,13 +259,39 @@ int fdog_server_submit(fdog_server* s, fdog_instance* inst, uint64_t* ticket) {
         inst->last_error = "a shard of a split instance runs through fdog_shard_pass";
         return FDOG_EUNSUPPORTED;
     }
-    // host work in the caller's thread: planning and the specialised kernels
+    Job* j = new (std::nothrow) Job();
+    if (!j) return FDOG_ENOMEM;
+    j->inst = inst;
+    if (!inst->planned && inst->params.planner != 1) {
+        // planned by the worker at admission, on the device where the builder takes it
+        j->plan_on_admit = true;
+        j->bytes = device_plan_bytes_bound(inst);
+        j->t_submit = now_s();
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->fatal != FDOG_OK) {
+            delete j;
+            return s->fatal;
+        }
+        j->ticket = s->next_ticket++;
+        s->jobs.emplace(j->ticket, j);
+        s->queue.push_back(j);
+        *ticket = j->ticket;
+        s->cv_work.notify_one();
+        return FDOG_OK;
+    }
+    // host planning in the caller's thread, and the specialised kernels
     int rc = plan(inst, false);
-    if (rc != FDOG_OK) return rc;
+    if (rc != FDOG_OK) {
+        delete j;
+        return rc;
+    }
     std::vector<int> ids = jit_ids(inst), added;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (s->fatal != FDOG_OK) return s->fatal;
+        if (s->fatal != FDOG_OK) {
+            delete j;
+            return s->fatal;
+        }
         for (int id : ids)
             if (std::find(s->jit_universe.begin(), s->jit_universe.end(), id) == s->jit_universe.end()) {
                 s->jit_universe.push_back(id);
@@ -252,12 +309,10 @@ int fdog_server_submit(fdog_server* s, fdog_instance* inst, uint64_t* ticket) {
             for (int id : added)
                 s->jit_universe.erase(std::find(s->jit_universe.begin(), s->jit_universe.end(), id));
             inst->last_error = why;
+            delete j;
             return rc;
         }
     }
-    Job* j = new (std::nothrow) Job();
-    if (!j) return FDOG_ENOMEM;
-    j->inst = inst;
     j->bytes = static_cast<int64_t>(arena_size(inst));
     j->t_submit = now_s();
     {

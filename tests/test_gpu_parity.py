@@ -533,6 +533,27 @@ def test_qap_evaluation_parity_full_size(P, oracle_mod):
     evaluation_parity(oracle_mod.Problem.from_ilp(g), inst)
 
 
+def test_qap_sparse_rounding_full_size(P, oracle_mod):
+    """The QAP-shaped workload with product terms between matches that are
+    10-NN neighbours on both sides: the full solve (Alg. 1 to the stopping
+    rule or 500 iterations, then Alg. 2) returns a feasible matching on the GPU,
+    as the oracle's does, whose objective is not below the bound; the two
+    rounded points are equal when the oracle's decisions have margin."""
+    g = ilpgen.qap(2, 500, 1000, 20, 10, sparse=True)
+    inst = P.Instance.from_ilp(g).build(0)
+    n, lb = inst.iterate(500)
+    rc, rounds = inst.primal_round()
+    x, obj, feas = inst.solution()
+    assert rc == P.FDOG_OK and feas and g.feasible(x), (rc, rounds)
+    assert abs(obj - g.objective(x)) <= 1e-9 * max(1.0, abs(obj)) and obj >= lb - 1e-6 * abs(lb)
+    orc = oracle_mod.Problem.from_ilp(g)
+    orc.iterate(n)  # the GPU's schedule: its dual iterations, then Alg. 2
+    r = orc.round()
+    assert r["status"] == 0 and g.feasible(r["x"])
+    if r["margin"] > 1e-3 * max(1.0, np.abs(g.cost).max()):
+        assert np.array_equal(x, r["x"]) and rounds == r["rounds"]
+
+
 def test_cell_batch_members_parity_full_size(P, oracle_mod):
     """The 64-instance cell-tracking batch at full size, solved as one batch
     with the autotuned launch shape (dual phase to the stopping rule, no

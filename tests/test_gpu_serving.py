@@ -99,3 +99,27 @@ def test_release_and_build_again(P):
     x2, obj2, feas2 = inst.solution()
     assert np.array_equal(x, x2) and obj == obj2 and feas == feas2
     inst.close()
+
+
+def test_server_plans_requests_on_admission(P):
+    """Requests submitted unplanned are planned by the worker when it admits
+    them (on the device where the device builder takes them), with results
+    equal to the solo ones; a request whose rows cannot be satisfied reports
+    it as its status instead of failing the submission."""
+    g = ilpgen.mrf_grid(24, 24, 4, 5)
+    rb = ilpgen._RowBuilder()
+    rb.add([0, 1], [1, 1], 0, 3)  # x0 + x1 = 3: no assignment satisfies it
+    bad = rb.finish(2, [1.0, -1.0], "infeasible")
+    ref = solo(P, g, 200)
+    srv = P.Server(0, max_iters=200)
+    t = srv.submit(P.Instance.from_ilp(g))
+    tb = srv.submit(P.Instance.from_ilp(bad))
+    assert srv.wait(t, 300) and srv.wait(tb, 300)
+    assert srv.poll(tb)["status"] == P.FDOG_EINFEASIBLE
+    st = srv.poll(t)
+    inst = srv.take(t)
+    assert inst.plan_stats()[0]  # built by the device builder
+    x, obj, feas = inst.solution()
+    assert st["status"] == ref[0] and np.array_equal(x, ref[2]) and obj == ref[3] and feas == ref[4]
+    assert srv.stats()["hbm_used"] == 0
+    srv.close()

@@ -584,6 +584,9 @@ def lb_star_section(torch, P, g, dev, stream):
     tr = np.array([inst.iterate(1)[1] for _ in range(iters)])
     hit = np.nonzero(tr >= lb_star - 1e-4 * abs(lb_star))[0]
     k = int(hit[0]) + 1 if len(hit) else None
+    # the first iteration at which Alg. 1's stopping rule (window 10, tol 1e-4, at least 20 iterations)
+    # holds on this trajectory
+    rule = [t + 1 for t in range(19, iters) if tr[t] - tr[t - 10] <= 1e-4 * max(abs(tr[t]), 1.0)]
     inst.reset()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -591,7 +594,10 @@ def lb_star_section(torch, P, g, dev, stream):
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     inst.close()
+    rise = float(rec["lb_after_2000"]) - float(rec["lb_after_1500"]) if "lb_after_1500" in rec else None
     return {"lb_star": lb_star, "lb_star_source": f"FP64 oracle, {iters} iterations of Alg. 1 (omega 0.5), stored",
+            "lb_star_converged": False, "lb_star_rise_last_500_iters": rise,
+            "stop_rule_iter": rule[0] if rule else "not reached",
             "iters_to_1e-4": k, "seconds_to_1e-4": t if k else None,
             "gpu_bound_after_same_iters": float(tr[-1]),
             "gpu_vs_oracle_rel_diff": abs(float(tr[-1]) - lb_star) / max(1.0, abs(lb_star))}

@@ -473,8 +473,10 @@ void fdog_server_destroy(fdog_server* srv);
  * shards.
  *
  * fdog_shard_plan (host only): splits rows 0..n_rows-1 of an ILP in the
- * fdog_create form into n_shards contiguous blocks with about equal numbers
- * of non-zero entries: row_shard[j] (n_rows), copies[i] = |J_i|, the rows
+ * fdog_create form into n_shards blocks with about equal numbers of non-zero
+ * entries, contiguous in the order of each row's smallest variable (ties by
+ * row index), so that rows over nearby variables share a shard:
+ * row_shard[j] (n_rows), copies[i] = |J_i|, the rows
  * with a non-zero coefficient on variable i (n_vars), shared[i] = 1 when
  * rows of more than one shard hold i (n_vars).  coef may be NULL (every entry
  * counts).  FDOG_EINVAL on a malformed CSR or n_shards < 1.

@@ -150,19 +150,36 @@ int fdog_shard_plan(int32_t n_vars, int32_t n_rows, const int64_t* row_ptr, cons
     if (nnz > 0 && !col) return FDOG_EINVAL;
     for (int64_t q = 0; q < nnz; ++q)
         if (col[q] < 0 || col[q] >= n_vars) return FDOG_EINVAL;
-    // contiguous blocks of rows with about equal numbers of non-zero entries:
-    // a row goes to the shard that holds the midpoint of its entries
-    std::vector<int64_t> pre(static_cast<size_t>(n_rows) + 1, 0);
+    // Rows in the order of their smallest variable (ties by row index), cut
+    // into contiguous blocks of that order with about equal numbers of
+    // non-zero entries: a row goes to the shard that holds the midpoint of its
+    // entries.  Rows over nearby variables (a grid node's rows, a frame's
+    // rows) land in one shard, so the shards share few variables when the
+    // variables are numbered by locality.
+    std::vector<int32_t> key(static_cast<size_t>(n_rows)), order(static_cast<size_t>(n_rows));
+    std::vector<int64_t> len(static_cast<size_t>(n_rows));
     for (int32_t j = 0; j < n_rows; ++j) {
+        int32_t k = n_vars;
         int64_t c = 0;
-        for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q) c += (!coef || coef[q] != 0);
-        pre[j + 1] = pre[j] + c;
+        for (int64_t q = row_ptr[j]; q < row_ptr[j + 1]; ++q)
+            if (!coef || coef[q] != 0) {
+                k = std::min(k, col[q]);
+                ++c;
+            }
+        key[j] = k;
+        len[j] = c;
+        order[j] = j;
     }
-    const int64_t total = pre[n_rows];
-    for (int32_t j = 0; j < n_rows; ++j) {
-        int64_t s = total > 0 ? (pre[j] + pre[j + 1]) * n_shards / (2 * total)
-                              : static_cast<int64_t>(j) * n_shards / std::max(n_rows, 1);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    int64_t total = 0;
+    for (int32_t j = 0; j < n_rows; ++j) total += len[j];
+    int64_t before = 0;
+    for (int32_t r = 0; r < n_rows; ++r) {
+        const int32_t j = order[r];
+        int64_t s = total > 0 ? (2 * before + len[j]) * n_shards / (2 * total)
+                              : static_cast<int64_t>(r) * n_shards / std::max(n_rows, 1);
         row_shard[j] = static_cast<int32_t>(std::min<int64_t>(s, n_shards - 1));
+        before += len[j];
     }
     std::vector<int32_t> first(static_cast<size_t>(n_vars), -1);
     for (int32_t i = 0; i < n_vars; ++i) {

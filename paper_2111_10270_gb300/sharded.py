@@ -1,8 +1,9 @@
 """One instance split over several ranks (one process and one GPU per rank).
 
 Host side of the library's shard calls (fdog_shard_* in fastdog.h): the
-rows are split into contiguous blocks (fdog_shard_plan), each rank builds an
-ordinary instance of its block's rows, and every pass of Alg. 1 ends with an
+rows are split into blocks by their smallest variable (fdog_shard_plan),
+each rank builds an ordinary instance of its block's rows, and every pass of
+Alg. 1 ends with an
 all-reduce of one float per variable whose copies lie in several shards (the
 partial sums of its multipliers, from which each shard forms the deferred
 term of Eq. 5), every iteration with an all-reduce of the lower bound.  The

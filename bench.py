@@ -306,6 +306,40 @@ def batched_section(torch, P, dev, stream, params, n_inst, threads):
     batch.close()
     for i in insts:
         i.close()
+
+    # the persistent kernel (one cooperative launch per chunk of iterations) against graph replays of the
+    # per-pass kernels, both on the generic kernels, which are the persistent kernel's scope
+    generic = [P.Instance.from_ilp(g, P.capi.default_params(tol=params.tol, jit=-1)).build(dev, stream)
+               for g in ilps]
+    timed = {}
+    for mode in ("per_pass", "persistent"):
+        b = P.Batch(generic, stream)
+        if mode == "persistent":
+            b.set_persistent(True)
+
+        def run():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i in generic:
+                i.reset()
+            it, rd, st = b.solve(max_iters)
+            out = [(int(it[q]), int(rd[q]), int(st[q])) + tuple(generic[q].solution()[1:]) for q in range(n_inst)]
+            xs = [generic[q].solution()[0] for q in range(n_inst)]
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, out, xs
+
+        run()  # warm-up
+        timed[mode] = run()
+        b.close()
+    for i in generic:
+        i.close()
+    pp, pe = timed["per_pass"], timed["persistent"]
+    persistent = {
+        "kernels": "generic (params.jit = -1) for both",
+        "per_pass_instances_per_s": n_inst / pp[0], "persistent_instances_per_s": n_inst / pe[0],
+        "persistent_over_per_pass": pp[0] / pe[0],
+        "results_identical": bool(pp[1] == pe[1] and all(np.array_equal(a, c) for a, c in zip(pp[2], pe[2]))),
+    }
     return {
         "workload": f"cell-tracking batch: {n_inst} instances, frames U{{10..80}}, detections/frame U{{200..2000}}, "
                     f"seed 3 ({n_vars} variables in all)",
@@ -319,6 +353,7 @@ def batched_section(torch, P, dev, stream, params, n_inst, threads):
         "dual_iters_p50": pct([r[0] for r in seq], 50), "dual_iters_max": max(r[0] for r in seq),
         "plan_s_p50": pct([t for _, t in plan_stats], 50),
         "planned_on_device": sum(1 for od, _ in plan_stats if od),
+        "persistent_kernel": persistent,
     }
 
 

@@ -407,6 +407,22 @@ int fdog_profile_read(fdog_instance* inst, int64_t* sweep_launches, double* swee
  */
 typedef struct fdog_batch fdog_batch;
 int fdog_batch_create(fdog_instance* const* insts, int32_t n, void* cuda_stream, fdog_batch** out);
+/*
+ * fdog_batch_set_persistent (no counterpart in the paper: a way to run the
+ * batch): on = 1 runs each chunk of dual iterations of fdog_batch_solve as
+ * one persistent cooperative kernel whose blocks stay resident and pass the
+ * device-wide barriers of Alg. 1 (after each pass, after the deferred sums,
+ * after the bound) through a grid barrier of their own, instead of graph
+ * replays of per-pass kernels; on = 0 returns to the graph replays.  Results
+ * are the same bit for bit.  A block that waits at a barrier longer than
+ * barrier_wait_s seconds (0: 1 s) gives up: every block leaves the kernel,
+ * the members' control blocks carry the error and fdog_batch_solve returns
+ * FDOG_ETIMEOUT (the context stays usable; fdog_reset_dual clears the
+ * members).  Takes batches whose BDDs all have width <= 2 and run on the
+ * generic kernels (params.jit = -1 on every member): FDOG_EUNSUPPORTED
+ * otherwise.  FDOG_EINVAL for a bad flag or a negative wait.
+ */
+int fdog_batch_set_persistent(fdog_batch* batch, int32_t on, double barrier_wait_s);
 int fdog_batch_solve(fdog_batch* batch, int32_t max_iters, int32_t* iters, int32_t* rounds, int32_t* status);
 int fdog_batch_info(fdog_batch* batch, int32_t* warps_per_block, int32_t* chunk, int64_t* kernel_launches);
 const char* fdog_batch_last_error(const fdog_batch* batch);

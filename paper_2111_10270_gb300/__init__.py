@@ -7,6 +7,6 @@ calls.  There is no CPU fallback: using the binding without the compiled
 library raises.
 """
 from .capi import (  # noqa: F401
-    FDOG_EINFEASIBLE, FDOG_EINVAL, FDOG_ENOCONVERGE, FDOG_ENOMEM, FDOG_EQ, FDOG_ESTATE, FDOG_EUNSUPPORTED, FDOG_GE,
-    FDOG_LE, FDOG_OK, Batch, FdogError, Instance, Params, Server, lib, library_path,
+    FDOG_ECUDA, FDOG_EINFEASIBLE, FDOG_EINVAL, FDOG_ENOCONVERGE, FDOG_ENOMEM, FDOG_EQ, FDOG_ESTATE, FDOG_ETIMEOUT,
+    FDOG_EUNSUPPORTED, FDOG_GE, FDOG_LE, FDOG_OK, Batch, FdogError, Instance, Params, Server, lib, library_path,
 )

@@ -92,6 +92,7 @@ SIGNATURES = {
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "fdog_batch_create": (ctypes.c_int, [_P, _i32, _P, ctypes.POINTER(_P)]),
     "fdog_batch_solve": (ctypes.c_int, [_P, _i32, _P, _P, _P]),
+    "fdog_batch_set_persistent": (ctypes.c_int, [_P, _i32, _f64]),
     "fdog_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "fdog_batch_last_error": (ctypes.c_char_p, [_P]),
     "fdog_batch_destroy": (None, [_P]),
@@ -449,6 +450,14 @@ class Batch:
             detail = self._L.fdog_batch_last_error(self._h)
             raise FdogError(rc, "fdog_batch_solve", detail.decode() if detail else "")
         return iters, rounds, status
+
+    def set_persistent(self, on: bool = True, barrier_wait_s: float = 0.0):
+        """fdog_batch_set_persistent: dual iterations as one persistent kernel per chunk."""
+        rc = self._L.fdog_batch_set_persistent(self._h, 1 if on else 0, float(barrier_wait_s))
+        if rc != FDOG_OK:
+            detail = self._L.fdog_batch_last_error(self._h)
+            raise FdogError(rc, "fdog_batch_set_persistent", detail.decode() if detail else "")
+        return self
 
     def info(self):
         w, c, k = _i32(), _i32(), _i64()

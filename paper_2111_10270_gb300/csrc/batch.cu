@@ -88,6 +88,31 @@ int fdog_batch_solve(fdog_batch* b, int32_t max_iters, int32_t* iters, int32_t* 
     return FDOG_OK;
 }
 
+int fdog_batch_set_persistent(fdog_batch* b, int32_t on, double barrier_wait_s) {
+    if (!b || (on != 0 && on != 1) || barrier_wait_s < 0.0) return FDOG_EINVAL;
+    if (on) {
+        int prev = -1;
+        cudaGetDevice(&prev);
+        if (prev != b->device) cudaSetDevice(b->device);
+        BatchView v;
+        int rc = view_build(b->engine, v, b->members);
+        const bool ok = rc == FDOG_OK && persist_supported(v.b);
+        if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+        if (rc != FDOG_OK) {
+            b->last_error = b->engine.err;
+            return rc;
+        }
+        if (!ok) {
+            b->last_error = "the persistent kernel takes batches whose BDDs all have width <= 2 on the generic "
+                            "kernels (params.jit = -1)";
+            return FDOG_EUNSUPPORTED;
+        }
+    }
+    b->engine.persistent = on != 0;
+    b->engine.persist_wait_s = barrier_wait_s > 0.0 ? barrier_wait_s : 1.0;
+    return FDOG_OK;
+}
+
 int fdog_batch_info(fdog_batch* b, int32_t* warps_per_block, int32_t* chunk, int64_t* kernel_launches) {
     if (!b) return FDOG_EINVAL;
     if (warps_per_block) *warps_per_block = b->engine.cfg.warps_per_block;

@@ -29,6 +29,7 @@ BatchView::~BatchView() {
 }
 
 Engine::~Engine() {
+    if (dev_bar) cudaFree(dev_bar);
     if (dev_status) cudaFree(dev_status);
     if (host_status) cudaFreeHost(host_status);
     side.destroy();
@@ -203,6 +204,22 @@ int view_op(Engine& e, BatchView& v, int op, int arg) {
 
 int view_iterate(Engine& e, BatchView& v, int k) {
     if (k <= 0 || v.b.n_inst == 0) return FDOG_OK;
+    if (e.persistent && !(e.prof && e.prof->on) && persist_supported(v.b)) {
+        // the k iterations as one cooperative launch with grid barriers
+        if (!e.dev_bar && cudaMalloc(reinterpret_cast<void**>(&e.dev_bar), 4 * sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            e.dev_bar = nullptr;
+            e.err = "barrier state allocation failed";
+            return FDOG_ENOMEM;
+        }
+        const cudaError_t pe = launch_persistent(v.b, k, e.dev_bar, e.persist_wait_s, e.cfg, e.stream);
+        if (pe != cudaSuccess) {
+            cudaGetLastError();
+            e.err = std::string("persistent iterations: ") + cudaGetErrorString(pe);
+            return FDOG_ECUDA;
+        }
+        return FDOG_OK;
+    }
     // graphs need a capturable stream and are skipped while per-launch timing is on
     const bool graphs = e.chunk > 1 && e.stream != nullptr && !(e.prof && e.prof->on);
     int direct = k;

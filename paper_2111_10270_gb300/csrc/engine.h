@@ -49,6 +49,11 @@ struct Engine {
     InstStatus* host_status = nullptr;  // pinned
     int status_cap = 0;
     SideStreams side;  // created by engine_use_side; cfg.side points here once they exist
+    // dual iterations as one persistent cooperative kernel per chunk (persist.cu) instead of graph
+    // replays of per-pass kernels, for views it supports; barrier waits end after persist_wait_s
+    bool persistent = false;
+    double persist_wait_s = 1.0;
+    unsigned* dev_bar = nullptr;  // the persistent kernel's barrier state
     std::string err;
     ~Engine();
 };

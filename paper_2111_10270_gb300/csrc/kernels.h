@@ -167,6 +167,16 @@ cudaError_t launch_round_apply(const DevBatch& b, const LaunchCfg& cfg, cudaStre
 cudaError_t launch_objective(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_accept(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 
+// The persistent iteration kernel (persist.cu): `iters` dual iterations of
+// every member as one cooperative launch, phases separated by a grid barrier
+// whose waits end after wait_s seconds (then every member's control block
+// carries error 1).  bar: 3 device words of barrier state.  Views whose tiles
+// all lie in the generic width-2 classes only (persist_supported).
+bool persist_supported(const DevBatch& b);
+size_t persist_smem_bytes(const DevBatch& b);
+cudaError_t launch_persistent(const DevBatch& b, int iters, unsigned* bar, double wait_s, const LaunchCfg& cfg,
+                              cudaStream_t s);
+
 // one full dual iteration (forward pass, deferred sums, backward pass,
 // deferred sums, lower bound) on every instance of the batch
 cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);

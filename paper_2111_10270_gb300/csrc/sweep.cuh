@@ -140,18 +140,22 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs& a, int g, int lan
     _Pragma("unroll") for (int tt = 0; tt < (REG ? kRegK : k); ++tt) \
         if (const int t = (REG ? kRegK : k) - 1 - tt; t < k)
 
+// shared-memory floats one warp of sweep_tile uses
+template <int W, bool REG>
+__host__ __device__ __forceinline__ size_t sweep_warp_floats(const SweepArgs& a) {
+    return (REG ? 0 : static_cast<size_t>(a.kstride) * kTile * (2 + W)) + static_cast<size_t>(a.epi) * kTile * 2;
+}
+
+// One tile g of a class (lane = BDD), the warp's shared memory at wsm; the
+// tile this warp visits next (g_next, if below a.total) is prefetched into L2.
 template <int W, bool REG, int MODE>
-__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
-        prefetch_tile(a, g + gridDim.x * wpb, lane);
+__device__ __forceinline__ void sweep_tile(const SweepArgs& a, int g, int g_next, float* wsm, int lane) {
+    {
+        prefetch_tile(a, g_next, lane);
         const int ii = find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
-            if (FDOG_INACTIVE(I->ctl)) continue;  // stopped, or out of iterations
+            if (FDOG_INACTIVE(I->ctl)) return;  // stopped, or out of iterations
         }
         const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
         const ShapeDev sh = I->shapes[tile.shape];
@@ -165,9 +169,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 
         Store<W, REG> S;
         // per-warp shared memory: [Store arrays (shared-memory variants)] [staging for tile-local sums]
-        const size_t warp_floats =
-            (REG ? 0 : static_cast<size_t>(a.kstride) * kTile * (2 + W)) + static_cast<size_t>(a.epi) * kTile * 2;
-        float* wsm = smem + static_cast<size_t>(wib) * warp_floats;
         if constexpr (!REG) {
             S.base = wsm + lane;
             S.stride = a.kstride;
@@ -351,6 +352,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     }
 }
 
+template <int W, bool REG, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    float* wsm = smem + static_cast<size_t>(wib) * sweep_warp_floats<W, REG>(a);
+    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb)
+        sweep_tile<W, REG, MODE>(a, g, g + gridDim.x * wpb, wsm, lane);
+}
+
 
 // Long rows (more than kRegK layers) of narrow BDDs (W <= kRegW).  Staging
 // every layer in shared memory would size each warp's region by the longest
@@ -364,24 +376,24 @@ __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
 // extra label sweep over data the warp has just read.
 // Shared memory per warp: a.kstride checkpoints x W labels x 32 lanes, then
 // the tile-local staging (a.epi layers).
+// shared-memory floats one warp of seg_tile uses
+template <int W>
+__host__ __device__ __forceinline__ size_t seg_warp_floats(const SweepArgs& a) {
+    return static_cast<size_t>(a.kstride) * W * kTile + static_cast<size_t>(a.epi) * kTile * 2;
+}
+
 template <int W, int MODE>
-__global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
+__device__ __forceinline__ void seg_tile(const SweepArgs& a, int g, int g_next, float* wsm, int lane) {
     constexpr int C = kRegK;
-    extern __shared__ float smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
-    const size_t warp_floats = static_cast<size_t>(a.kstride) * W * kTile + static_cast<size_t>(a.epi) * kTile * 2;
-    float* wsm = smem + static_cast<size_t>(wib) * warp_floats;
     float* cp = wsm + lane;  // checkpoint s, label v at cp[(s * W + v) * kTile]
     float* ep_lam = wsm + static_cast<size_t>(a.kstride) * W * kTile;
     int* ep_var = reinterpret_cast<int*>(ep_lam + static_cast<size_t>(a.epi) * kTile);
-    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb) {
-        prefetch_tile(a, g + gridDim.x * wpb, lane);
+    {
+        prefetch_tile(a, g_next, lane);
         const int ii = find_inst(a.prefix, a.n_inst, g);
         const InstDev* __restrict__ I = a.insts + ii;
         if constexpr (MODE == kFwdUpdate || MODE == kBwdUpdate) {
-            if (FDOG_INACTIVE(I->ctl)) continue;
+            if (FDOG_INACTIVE(I->ctl)) return;
         }
         const TileDev tile = I->tiles[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))];
         const ShapeDev sh = I->shapes[tile.shape];
@@ -694,6 +706,17 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
             if (lane == 0) I->tile_lb[__ldg(a.first + ii) + (g - __ldg(a.prefix + ii))] = make_float2(s, comp);
         }
     }
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
+    extern __shared__ float smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    float* wsm = smem + static_cast<size_t>(wib) * seg_warp_floats<W>(a);
+    for (int g = blockIdx.x * wpb + wib; g < a.total; g += gridDim.x * wpb)
+        seg_tile<W, MODE>(a, g, g + gridDim.x * wpb, wsm, lane);
 }
 
 #undef FD_UP

@@ -89,3 +89,87 @@ def test_batch_autotuner_picks_a_block_size(P):
     b = P.Batch(insts)
     info = b.info()
     assert info["warps_per_block"] in (2, 4, 8) and info["chunk"] >= 1
+
+
+def width2_instances():
+    """Instances whose BDDs all have width <= 2 (the persistent kernel's scope):
+    MRF grids, cell tracking with long in-flow rows (segmented kernel), and
+    matchings with products of neighbour matches."""
+    return [ilpgen.mrf_grid(8, 8, 3, 0), ilpgen.mrf_grid(12, 10, 4, 1, potts_max=2.0), ilpgen.mrf_grid(16, 16, 2, 2),
+            ilpgen.mrf_grid(5, 7, 5, 3), ilpgen.cell_tracking(12, 5, 20, 60), ilpgen.cell_tracking(4, 4, 20, 40),
+            ilpgen.qap(3, 20, 40, 6, 3, sparse=True), ilpgen.qap(5, 30, 60, 8, 4, sparse=True)]
+
+
+def batch_results(P, ilps, stream, persistent, max_iters=150):
+    insts = [P.Instance.from_ilp(g, jit=-1).build(0, stream) for g in ilps]
+    batch = P.Batch(insts, stream)
+    if persistent:
+        batch.set_persistent(True)
+    iters, rounds, status = batch.solve(max_iters)
+    out = []
+    for q, inst in enumerate(insts):
+        x, obj, feas = inst.solution()
+        out.append((int(iters[q]), int(rounds[q]), int(status[q]), x.tobytes(), obj, feas,
+                    inst.multipliers()[2].tobytes(), inst.lower_bound()))
+    batch.close()
+    return out
+
+
+@pytest.mark.parametrize("use_stream", [False, True], ids=["default-stream", "own-stream"])
+def test_persistent_batch_equals_graph_batch(P, use_stream):
+    """The persistent kernel (one cooperative launch per chunk of iterations,
+    grid barriers between the passes) gives bit for bit the results of the
+    per-pass kernels: iterations, rounds, statuses, solutions, objectives,
+    multipliers and bounds."""
+    import torch
+
+    stream = torch.cuda.Stream() if use_stream else None
+    ilps = width2_instances()
+    graph = batch_results(P, ilps, stream, False)
+    persistent = batch_results(P, ilps, stream, True)
+    for q, (a, b) in enumerate(zip(graph, persistent)):
+        assert a == b, (q, a[:3], b[:3])
+
+
+def test_persistent_barrier_wait_runs_out(P):
+    """A barrier wait limit far below the time the blocks need to meet makes
+    the waits run out: the solve returns FDOG_ETIMEOUT without faulting, and
+    after a reset the same members solve normally on the per-pass kernels."""
+    ilps = width2_instances()[:4]
+    ref = batch_results(P, ilps, None, False)
+    insts = [P.Instance.from_ilp(g, jit=-1).build(0) for g in ilps]
+    batch = P.Batch(insts).set_persistent(True, barrier_wait_s=1e-9)
+    with pytest.raises(P.FdogError) as e:
+        batch.solve(150)
+    assert e.value.code == P.FDOG_ETIMEOUT
+    for inst in insts:
+        inst.reset()
+    batch.set_persistent(False)
+    iters, rounds, status = batch.solve(150)
+    for q, inst in enumerate(insts):
+        x, obj, feas = inst.solution()
+        got = (int(iters[q]), int(rounds[q]), int(status[q]), x.tobytes(), obj, feas,
+               inst.multipliers()[2].tobytes(), inst.lower_bound())
+        assert got == ref[q], q
+    batch.close()
+
+
+def test_persistent_batch_scope(P):
+    """Shape-specialised kernels or BDDs wider than 2 are outside the
+    persistent kernel: FDOG_EUNSUPPORTED, and the batch keeps the per-pass
+    kernels."""
+    insts = [P.Instance.from_ilp(ilpgen.mrf_grid(8, 8, 3, 0), jit=1).build(0)]
+    batch = P.Batch(insts)
+    with pytest.raises(P.FdogError) as e:
+        batch.set_persistent(True)
+    assert e.value.code == P.FDOG_EUNSUPPORTED
+    batch.close()
+    wide = mixed_instances()[4]  # cardinality rows: widths up to 9
+    insts = [P.Instance.from_ilp(wide, jit=-1).build(0)]
+    batch = P.Batch(insts)
+    with pytest.raises(P.FdogError) as e:
+        batch.set_persistent(True)
+    assert e.value.code == P.FDOG_EUNSUPPORTED
+    iters, _, _ = batch.solve(20)
+    assert iters[0] > 0
+    batch.close()

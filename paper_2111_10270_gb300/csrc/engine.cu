@@ -493,33 +493,62 @@ int view_autotune(Engine& e, BatchView& v, bool tune_grid) {
     float best_ms = 1e30f;
     LaunchCfg cfg = e.cfg;
     cfg.prof = nullptr;
+    // The candidates are timed on real update passes: each member's
+    // multipliers and deferred terms are saved in its min-marginal and
+    // perturbation scratch arrays (which nothing reads before they are next
+    // written) and its control block in its pinned host copy, the iteration
+    // limits are opened for the trials, and all of it is restored afterwards,
+    // so the dual state is unchanged.
+    cudaError_t ce = cudaSuccess;
+    auto save = [&](bool back) {
+        for (fdog_instance* m : v.members) {
+            if (ce == cudaSuccess) {
+                ce = back ? cudaMemcpyAsync(m->dev.ctl, m->host_ctl, sizeof(InstCtl), cudaMemcpyHostToDevice, e.stream)
+                          : cudaMemcpyAsync(m->host_ctl, m->dev.ctl, sizeof(InstCtl), cudaMemcpyDeviceToHost, e.stream);
+                (back ? m->h2d_bytes : m->d2h_bytes) += static_cast<int64_t>(sizeof(InstCtl));
+            }
+            if (m->dec.n_bdds == 0 || ce != cudaSuccess) continue;
+            const size_t nl = sizeof(float) * static_cast<size_t>(m->dec.slots_pad);
+            const size_t nt = sizeof(float) * static_cast<size_t>(m->n_vars);
+            ce = back ? cudaMemcpyAsync(m->dev.lam, m->dev.mm0, nl, cudaMemcpyDeviceToDevice, e.stream)
+                      : cudaMemcpyAsync(m->dev.mm0, m->dev.lam, nl, cudaMemcpyDeviceToDevice, e.stream);
+            if (ce == cudaSuccess)
+                ce = back ? cudaMemcpyAsync(m->dev.T, m->dev.pert, nt, cudaMemcpyDeviceToDevice, e.stream)
+                          : cudaMemcpyAsync(m->dev.pert, m->dev.T, nt, cudaMemcpyDeviceToDevice, e.stream);
+        }
+    };
+    save(false);
+    int rc = ce == cudaSuccess ? view_op(e, v, kOpLimit, 1 << 30) : FDOG_OK;
     // warps per block x grid mode (one persistent wave, or a block per tile group)
-    for (int combo = 0; combo < (tune_grid ? 6 : 3); ++combo) {
+    for (int combo = 0; combo < (tune_grid ? 6 : 3) && ce == cudaSuccess && rc == FDOG_OK; ++combo) {
         const int wpb = 2 << (combo % 3), waves = tune_grid ? (combo < 3 ? 1 : 0) : e.cfg.max_waves;
         cfg.warps_per_block = wpb;
         cfg.max_waves = waves;
-        cudaError_t ce = launch_sweep(v.b, kMinMarg, 0, cfg, e.stream);  // warm-up
+        ce = launch_sweep(v.b, kFwdUpdate, 0, cfg, e.stream);  // warm-up
         if (ce == cudaSuccess) ce = cudaEventRecord(a, e.stream);
-        for (int r = 0; r < 3 && ce == cudaSuccess; ++r) ce = launch_sweep(v.b, kMinMarg, 0, cfg, e.stream);
+        for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
+            ce = launch_sweep(v.b, kFwdUpdate, 0, cfg, e.stream);
+            if (ce == cudaSuccess) ce = launch_sweep(v.b, kBwdUpdate, 0, cfg, e.stream);
+        }
         if (ce == cudaSuccess) ce = cudaEventRecord(z, e.stream);
         if (ce == cudaSuccess) ce = cudaEventSynchronize(z);
         float ms = 0.f;
         if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, z);
-        if (ce != cudaSuccess) {
-            cudaEventDestroy(a);
-            cudaEventDestroy(z);
-            return fail(e, ce, "autotune");
-        }
-        if (ms < best_ms) { best_ms = ms; best = wpb; best_waves = waves; }
+        if (ce == cudaSuccess && ms < best_ms) { best_ms = ms; best = wpb; best_waves = waves; }
     }
+    save(true);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e.stream);
     cudaEventDestroy(a);
     cudaEventDestroy(z);
+    if (ce != cudaSuccess) return fail(e, ce, "autotune");
+    if (rc != FDOG_OK) return rc;
     e.cfg.warps_per_block = best;
     e.cfg.max_waves = best_waves;
     // iterations per graph replay: about 1 ms of device work per replay (an
-    // iteration costs about two and a half sweeps), so that the status read
-    // after a replay stays a small fraction of it; results do not depend on it
-    const double iter_ms = 2.5 * best_ms / 3.0;
+    // iteration costs about two and a half sweeps; four sweeps were timed), so
+    // that the status read after a replay stays a small fraction of it;
+    // results do not depend on it
+    const double iter_ms = 2.5 * best_ms / 4.0;
     int chunk = 4;
     while (chunk < 32 && chunk * iter_ms < 1.0) chunk *= 2;
     e.chunk = chunk;

@@ -94,9 +94,10 @@ int engine_admit(Engine& e, std::vector<Member>& ms, size_t first, int max_iters
 int engine_step(Engine& e, std::vector<Member>& ms);
 
 // Picks the sweep kernels' warps per block and grid mode for this view by
-// timing min-marginal sweeps (they write only scratch, so the dual state is
-// untouched), and the iterations per graph replay from the measured sweep
-// time; results depend on none of the three.
+// timing ascending and descending update passes (each member's multipliers
+// and deferred terms are saved in scratch arrays and restored, so the dual
+// state is unchanged), and the iterations per graph replay from the
+// measured sweep time; results depend on none of the three.
 int view_autotune(Engine& e, BatchView& v, bool tune_grid = true);
 
 // Alg. 2 for every member (which must have finished their dual phase):

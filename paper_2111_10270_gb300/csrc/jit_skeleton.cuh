@@ -62,6 +62,10 @@ __device__ __forceinline__ void fdog_prefetch_tile(const SweepArgs& a, int g, in
 template <int MODE>
 __device__ __forceinline__ void fdog_jit_sweep(const SweepArgs& a) {
     extern __shared__ float fdog_smem[];
+    // programmatic dependent launch (the launches allow it): let the next kernel be scheduled once every
+    // block has started, and touch memory only after the kernel before this one has completed
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;

@@ -39,11 +39,15 @@ using dev::reduce_T_one;
 using dev::reduce_T_wide_one;
 
 __global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
+    dev::pdl_trigger();
+    dev::pdl_wait();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g < a.total) reduce_T_one(a, g);
 }
 
 __global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
+    dev::pdl_trigger();
+    dev::pdl_wait();
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (g < a.total) reduce_T_wide_one(a, g, threadIdx.x & 31);
 }
@@ -55,6 +59,8 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     __shared__ double ss[8], sc[8];
     __shared__ float ssf[8], scf[8];
     __shared__ int last;
+    dev::pdl_trigger();
+    dev::pdl_wait();
     const int g = blockIdx.x;
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
@@ -82,6 +88,8 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
 // and the stopping test.  Runs after the deferred sums of the backward pass,
 // which must still see the iteration as active.
 __global__ void lb_commit_kernel(const InstDev* insts, int n) {
+    dev::pdl_trigger();
+    dev::pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     InstCtl* ctl = insts[i].ctl;
@@ -390,21 +398,27 @@ bool can_fork(const LaunchCfg& cfg) { return cfg.side && cfg.side->ready; }
 
 cudaError_t launch_windowed(const void* fn, int blocks, int threads, void** args, size_t smem, cudaStream_t s,
                             const L2Window& l2) {
-    if (l2.bytes == 0) return cudaLaunchKernel(fn, dim3(blocks), dim3(threads), args, smem, s);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-    attr[0].val.accessPolicyWindow.base_ptr = l2.base;
-    attr[0].val.accessPolicyWindow.num_bytes = l2.bytes;
-    attr[0].val.accessPolicyWindow.hitRatio = l2.hit_ratio;
-    attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (l2.bytes > 0) {
+        attr[n].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[n].val.accessPolicyWindow.base_ptr = l2.base;
+        attr[n].val.accessPolicyWindow.num_bytes = l2.bytes;
+        attr[n].val.accessPolicyWindow.hitRatio = l2.hit_ratio;
+        attr[n].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[n].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        ++n;
+    }
     cudaLaunchConfig_t c{};
     c.gridDim = dim3(blocks);
     c.blockDim = dim3(threads);
     c.dynamicSmemBytes = smem;
     c.stream = s;
     c.attrs = attr;
-    c.numAttrs = 1;
+    c.numAttrs = n;
     return cudaLaunchKernelExC(&c, fn, args);
 }
 
@@ -517,11 +531,19 @@ cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_
         ws = cfg.side->s[0];
     }
     if (b.wide_total > 0) {
-        reduce_T_wide_kernel<<<(b.wide_total + 7) / 8, 256, 0, ws>>>(flat(b, b.wide_prefix, b.wide_total));
+        FlatArgs fa = flat(b, b.wide_prefix, b.wide_total);
+        void* args[] = {&fa};
+        const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_wide_kernel),
+                                              (b.wide_total + 7) / 8, 256, args, 0, ws, L2Window());
+        if (e != cudaSuccess) return e;
         cfg.count();
     }
     if (b.work_total > 0) {
-        reduce_T_kernel<<<(b.work_total + 255) / 256, 256, 0, s>>>(flat(b, b.work_prefix, b.work_total));
+        FlatArgs fa = flat(b, b.work_prefix, b.work_total);
+        void* args[] = {&fa};
+        const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_kernel),
+                                              (b.work_total + 255) / 256, 256, args, 0, s, L2Window());
+        if (e != cudaSuccess) return e;
         cfg.count();
     }
     if (fork) {
@@ -575,8 +597,10 @@ void Profiler::release() {
 cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s) {
     if (b.chunks_total == 0) return cudaSuccess;
     cfg.count();
-    lb_reduce_kernel<<<b.chunks_total, 256, 0, s>>>(LbArgs{b.insts, b.chunk_prefix, b.n_inst, target});
-    return cudaGetLastError();
+    LbArgs la{b.insts, b.chunk_prefix, b.n_inst, target};
+    void* args[] = {&la};
+    return launch_windowed(reinterpret_cast<const void*>(lb_reduce_kernel), b.chunks_total, 256, args, 0, s,
+                           L2Window());
 }
 
 cudaError_t launch_init(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
@@ -656,8 +680,11 @@ cudaError_t launch_status(const DevBatch& b, InstStatus* dev_out, const LaunchCf
 cudaError_t launch_lb_commit(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
     if (b.n_inst == 0) return cudaSuccess;
     cfg.count();
-    lb_commit_kernel<<<(b.n_inst + 127) / 128, 128, 0, s>>>(b.insts, b.n_inst);
-    return cudaGetLastError();
+    const InstDev* insts = b.insts;
+    int n = b.n_inst;
+    void* args[] = {&insts, &n};
+    return launch_windowed(reinterpret_cast<const void*>(lb_commit_kernel), (b.n_inst + 127) / 128, 128, args, 0, s,
+                           L2Window());
 }
 
 cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {

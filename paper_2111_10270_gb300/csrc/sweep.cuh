@@ -17,6 +17,16 @@
 namespace fdog {
 namespace dev {
 
+// Programmatic dependent launch.  The iteration kernels are launched with
+// programmatic stream serialization: a kernel may be scheduled while the one
+// before it on its stream drains.  pdl_wait() returns once that kernel has
+// completed and its writes are visible (at once for a launch without the
+// attribute), so every such kernel calls it before it touches memory;
+// pdl_trigger() lets the next kernel be scheduled once every block of this
+// one has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float finf() { return __int_as_float(0x7f800000); }
@@ -355,6 +365,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs& a, int g, int g_next
 template <int W, bool REG, int MODE>
 __global__ void __launch_bounds__(256) sweep_kernel(SweepArgs a) {
     extern __shared__ float smem[];
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -711,6 +723,8 @@ __device__ __forceinline__ void seg_tile(const SweepArgs& a, int g, int g_next, 
 template <int W, int MODE>
 __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
     extern __shared__ float smem[];
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
@@ -724,7 +738,9 @@ __global__ void __launch_bounds__(256) sweep_seg_kernel(SweepArgs a) {
 
 }  // namespace dev
 
-// a kernel launch with an optional L2 access-policy window (kernels.cu)
+// a kernel launch with programmatic stream serialization (the kernel calls
+// pdl_wait before it touches memory) and an optional L2 access-policy window
+// (kernels.cu)
 cudaError_t launch_windowed(const void* fn, int blocks, int threads, void** args, size_t smem, cudaStream_t s,
                             const L2Window& l2);
 

@@ -52,16 +52,13 @@ __global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
     if (g < a.total) reduce_T_wide_one(a, g, threadIdx.x & 31);
 }
 
-// One block per chunk of kLbChunk tiles, then the last block of the instance
-// sums the chunk partials.  The chunking depends only on the instance, so its
-// bound is the same alone or in a batch.
-__global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
+// One block per chunk of kLbChunk tiles (chunk g of the flat batch), then the
+// last block of the instance sums the chunk partials.  The chunking depends
+// only on the instance, so its bound is the same alone or in a batch.
+__device__ __forceinline__ void lb_reduce_block(const LbArgs& a, int g) {
     __shared__ double ss[8], sc[8];
     __shared__ float ssf[8], scf[8];
     __shared__ int last;
-    dev::pdl_trigger();
-    dev::pdl_wait();
-    const int g = blockIdx.x;
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
     InstCtl* ctl = I->ctl;
@@ -82,6 +79,27 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
         ctl->lb_staged = lb;
         ctl->staged = 1;
     }
+}
+
+__global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
+    dev::pdl_trigger();
+    dev::pdl_wait();
+    lb_reduce_block(a, blockIdx.x);
+}
+
+// The descending pass's deferred sums and its bound in one launch: the first
+// a.chunks blocks reduce the bound (lb_reduce_kernel's work), the rest form
+// the deferred terms (reduce_T_kernel's); both only read the pass's output
+// and write disjoint state, as when they run side by side on two streams.
+__global__ void __launch_bounds__(256) reduce_T_lb_kernel(FlatArgs f, LbArgs l, int chunks) {
+    dev::pdl_trigger();
+    dev::pdl_wait();
+    if (static_cast<int>(blockIdx.x) < chunks) {
+        lb_reduce_block(l, blockIdx.x);
+        return;
+    }
+    const int g = (blockIdx.x - chunks) * blockDim.x + threadIdx.x;
+    if (g < f.total) reduce_T_one(f, g);
 }
 
 // End of an iteration for every member whose bound was staged: ring, counter
@@ -594,6 +612,21 @@ void Profiler::release() {
     pool.clear();
 }
 
+cudaError_t launch_reduce_T_lb(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    const bool timed = cfg.prof && cfg.prof->on;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
+    FlatArgs fa = flat(b, b.work_prefix, b.work_total);
+    LbArgs la{b.insts, b.chunk_prefix, b.n_inst, kLbStage};
+    int chunks = b.chunks_total;
+    void* args[] = {&fa, &la, &chunks};
+    const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_lb_kernel),
+                                          chunks + (b.work_total + 255) / 256, 256, args, 0, s, L2Window());
+    cfg.count();
+    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(1, ev0, ev1); }
+    return e;
+}
+
 cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s) {
     if (b.chunks_total == 0) return cudaSuccess;
     cfg.count();
@@ -694,7 +727,12 @@ cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream
     if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_sweep(b, kBwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
     // the bound reduction and the deferred sums both read only the pass's output
-    // (tile partials, multipliers) and write disjoint state: side by side
+    // (tile partials, multipliers) and write disjoint state: one launch when there
+    // are no warp-per-variable sums, else side by side on two streams
+    if (b.chunks_total > 0 && b.work_total > 0 && b.wide_total == 0) {
+        if ((e = launch_reduce_T_lb(b, cfg, s)) != cudaSuccess) return e;
+        return launch_lb_commit(b, cfg, s);
+    }
     const bool fork = can_fork(cfg) && b.chunks_total > 0;
     if (fork) {
         if ((e = cudaEventRecord(cfg.side->fork, s)) != cudaSuccess) return e;

@@ -100,6 +100,9 @@ struct InstCtl {
     double tol;
     double delta;             // rounding: current perturbation strength
     double lb_staged;
+    int32_t pass_active;      // the instance's activity at the start of the running iteration, recorded
+                              // by its ascending pass's deferred sums for the end-of-iteration kernel
+    int32_t pad;
 };
 
 // True when the update kernels must leave the instance alone: its stopping

@@ -53,9 +53,11 @@ __global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
 }
 
 // One block per chunk of kLbChunk tiles (chunk g of the flat batch), then the
-// last block of the instance sums the chunk partials.  The chunking depends
-// only on the instance, so its bound is the same alone or in a batch.
-__device__ __forceinline__ void lb_reduce_block(const LbArgs& a, int g) {
+// last block of the instance sums the chunk partials and stages the bound for
+// lb_commit_kernel, or with `commit` commits the iteration itself.  The
+// chunking depends only on the instance, so its bound is the same alone or in
+// a batch.
+__device__ __forceinline__ void lb_reduce_block(const LbArgs& a, int g, bool commit) {
     __shared__ double ss[8], sc[8];
     __shared__ float ssf[8], scf[8];
     __shared__ int last;
@@ -76,35 +78,42 @@ __device__ __forceinline__ void lb_reduce_block(const LbArgs& a, int g) {
     const double lb = lb_total(I, ss, sc);
     if (threadIdx.x == 0) {
         ctl->ticket = 0;
-        ctl->lb_staged = lb;
-        ctl->staged = 1;
+        if (commit) {
+            commit_iteration(ctl, lb);
+        } else {
+            ctl->lb_staged = lb;
+            ctl->staged = 1;
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     dev::pdl_trigger();
     dev::pdl_wait();
-    lb_reduce_block(a, blockIdx.x);
+    lb_reduce_block(a, blockIdx.x, false);
 }
 
-// The descending pass's deferred sums and its bound in one launch: the first
-// a.chunks blocks reduce the bound (lb_reduce_kernel's work), the rest form
-// the deferred terms (reduce_T_kernel's); both only read the pass's output
-// and write disjoint state, as when they run side by side on two streams.
+// The end of an iteration in one launch: the first `chunks` blocks reduce the
+// descending pass's bound and the last of an instance's blocks commits the
+// iteration (ring, counter, stopping test); the other blocks form the deferred
+// terms of the pass.  Both only read the pass's output.  A commit may land
+// while the deferred sums run, so they test the instance's activity as the
+// ascending pass's deferred sums recorded it at the start of the iteration.
 __global__ void __launch_bounds__(256) reduce_T_lb_kernel(FlatArgs f, LbArgs l, int chunks) {
     dev::pdl_trigger();
     dev::pdl_wait();
     if (static_cast<int>(blockIdx.x) < chunks) {
-        lb_reduce_block(l, blockIdx.x);
+        lb_reduce_block(l, blockIdx.x, true);
         return;
     }
     const int g = (blockIdx.x - chunks) * blockDim.x + threadIdx.x;
-    if (g < f.total) reduce_T_one(f, g);
+    if (g < f.total) reduce_T_one<true>(f, g);
 }
 
 // End of an iteration for every member whose bound was staged: ring, counter
 // and the stopping test.  Runs after the deferred sums of the backward pass,
-// which must still see the iteration as active.
+// which must still see the iteration as active (views with warp-per-variable
+// sums and shards; the others commit inside reduce_T_lb_kernel).
 __global__ void lb_commit_kernel(const InstDev* insts, int n) {
     dev::pdl_trigger();
     dev::pdl_wait();
@@ -729,10 +738,7 @@ cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream
     // the bound reduction and the deferred sums both read only the pass's output
     // (tile partials, multipliers) and write disjoint state: one launch when there
     // are no warp-per-variable sums, else side by side on two streams
-    if (b.chunks_total > 0 && b.work_total > 0 && b.wide_total == 0) {
-        if ((e = launch_reduce_T_lb(b, cfg, s)) != cudaSuccess) return e;
-        return launch_lb_commit(b, cfg, s);
-    }
+    if (b.chunks_total > 0 && b.work_total > 0 && b.wide_total == 0) return launch_reduce_T_lb(b, cfg, s);
     const bool fork = can_fork(cfg) && b.chunks_total > 0;
     if (fork) {
         if ((e = cudaEventRecord(cfg.side->fork, s)) != cudaSuccess) return e;

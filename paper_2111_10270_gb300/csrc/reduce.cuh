@@ -27,12 +27,24 @@ struct FlatArgs {
 // the block scheduler keeps every warp slot busy); its slot positions come
 // from the bucket of its copy count, one coalesced column per copy, so all of
 // its multiplier gathers are issued together.
-// one listed variable with at most 8 copies (work index g of the flat batch)
+// one listed variable with at most 8 copies (work index g of the flat batch).
+// Instances whose stopping rule or iteration limit has stopped them are left
+// alone.  SNAPSHOT: the activity test reads InstCtl::pass_active, which the
+// ascending pass's deferred sums recorded (work index 0 of each instance),
+// instead of the control block's live state, which the end-of-iteration
+// kernel's commit may change while this runs.
+template <bool SNAPSHOT = false>
 __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
-    if (FDOG_INACTIVE(I->ctl)) return;
     const int w = g - __ldg(a.prefix + ii);  // below wb_start[FDOG_WBUCKETS - 1]: at most 8 copies
+    if (SNAPSHOT) {
+        if (!I->ctl->pass_active) return;
+    } else {
+        const bool inactive = FDOG_INACTIVE(I->ctl);
+        if (w == 0) I->ctl->pass_active = inactive ? 0 : 1;
+        if (inactive) return;
+    }
     const int i = __ldcs(I->work + w);  // a variable with copies in several tiles (list streamed once)
     int b = 0;
 #pragma unroll

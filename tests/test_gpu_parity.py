@@ -514,7 +514,14 @@ def test_early_stopping_rule(P, oracle_mod):
     # the oracle's bound satisfies the same rule within a couple of iterations of the stop
     stops = [t for t in range(20, len(tr)) if t + 1 > 10 and tr[t] - tr[t - 10] <= 1e-4 * max(1.0, abs(tr[t]))]
     assert stops and abs((stops[0] + 1) - n) <= 2
-    assert inst.iterate(10)[0] == 0  # stays stopped
+    # stays stopped, and further calls leave the state alone, before and after the add-back
+    lam0, lb0 = inst.multipliers()[2].tobytes(), inst.lower_bound()
+    assert inst.iterate(10)[0] == 0
+    assert inst.multipliers()[2].tobytes() == lam0 and inst.lower_bound() == lb0
+    inst.finalize()
+    lam1, lb1 = inst.multipliers()[2].tobytes(), inst.lower_bound()
+    assert inst.iterate(10)[0] == 0
+    assert inst.multipliers()[2].tobytes() == lam1 and inst.lower_bound() == lb1
 
 
 # ----------------------------------------------------------------------------

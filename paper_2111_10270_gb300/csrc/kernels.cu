@@ -38,20 +38,6 @@ using dev::neumaier;
 using dev::reduce_T_one;
 using dev::reduce_T_wide_one;
 
-__global__ void __launch_bounds__(256) reduce_T_kernel(FlatArgs a) {
-    dev::pdl_trigger();
-    dev::pdl_wait();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < a.total) reduce_T_one(a, g);
-}
-
-__global__ void __launch_bounds__(256) reduce_T_wide_kernel(FlatArgs a) {
-    dev::pdl_trigger();
-    dev::pdl_wait();
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (g < a.total) reduce_T_wide_one(a, g, threadIdx.x & 31);
-}
-
 // One block per chunk of kLbChunk tiles (chunk g of the flat batch), then the
 // last block of the instance sums the chunk partials and stages the bound for
 // lb_commit_kernel, or with `commit` commits the iteration itself.  The
@@ -93,27 +79,40 @@ __global__ void __launch_bounds__(256) lb_reduce_kernel(LbArgs a) {
     lb_reduce_block(a, blockIdx.x, false);
 }
 
-// The end of an iteration in one launch: the first `chunks` blocks reduce the
-// descending pass's bound and the last of an instance's blocks commits the
-// iteration (ring, counter, stopping test); the other blocks form the deferred
-// terms of the pass.  Both only read the pass's output.  A commit may land
-// while the deferred sums run, so they test the instance's activity as the
-// ascending pass's deferred sums recorded it at the start of the iteration.
-__global__ void __launch_bounds__(256) reduce_T_lb_kernel(FlatArgs f, LbArgs l, int chunks) {
+// One launch per deferred-sum step (Eq. 5's averaged term through Prop. 1).
+// Blocks [0, chunks) (END only): the descending pass's bound, and the last of
+// an instance's blocks commits the iteration (ring, counter, stopping test);
+// the next wide_blocks blocks: a warp per variable with more than 8 copies;
+// the rest: a thread per listed variable with at most 8 copies.  The parts
+// read only the pass's output and write disjoint state.  END: a commit may
+// land while the deferred sums run, so they test the instance's activity as
+// the ascending step recorded it at the start of the iteration.
+template <bool END>
+__global__ void __launch_bounds__(256) deferred_sum_kernel(FlatArgs work, FlatArgs wide, LbArgs l, int chunks,
+                                                           int wide_blocks) {
     dev::pdl_trigger();
     dev::pdl_wait();
-    if (static_cast<int>(blockIdx.x) < chunks) {
-        lb_reduce_block(l, blockIdx.x, true);
+    int blk = blockIdx.x;
+    if (END) {
+        if (blk < chunks) {
+            lb_reduce_block(l, blk, true);
+            return;
+        }
+        blk -= chunks;
+    }
+    if (blk < wide_blocks) {
+        const int g = (blk * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x)) >> 5;
+        if (g < wide.total) reduce_T_wide_one<END>(wide, g, threadIdx.x & 31);
         return;
     }
-    const int g = (blockIdx.x - chunks) * blockDim.x + threadIdx.x;
-    if (g < f.total) reduce_T_one<true>(f, g);
+    const int g = (blk - wide_blocks) * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+    if (g < work.total) reduce_T_one<END>(work, g);
 }
 
 // End of an iteration for every member whose bound was staged: ring, counter
 // and the stopping test.  Runs after the deferred sums of the backward pass,
-// which must still see the iteration as active (views with warp-per-variable
-// sums and shards; the others commit inside reduce_T_lb_kernel).
+// which must still see the iteration as active (the shards of a split
+// instance; whole instances commit inside deferred_sum_kernel<true>).
 __global__ void lb_commit_kernel(const InstDev* insts, int n) {
     dev::pdl_trigger();
     dev::pdl_wait();
@@ -544,41 +543,30 @@ static FlatArgs flat(const DevBatch& b, const int32_t* prefix, int total) {
     return FlatArgs{b.insts, prefix, b.n_inst, total};
 }
 
-cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
-    if (b.work_total == 0 && b.wide_total == 0) return cudaSuccess;
+// one deferred-sum step: END adds the bound reduction and the commit of the iteration
+static cudaError_t launch_deferred(const DevBatch& b, bool end, const LaunchCfg& cfg, cudaStream_t s) {
+    const int chunks = end ? b.chunks_total : 0;
+    if (b.work_total == 0 && b.wide_total == 0 && chunks == 0) return cudaSuccess;
     const bool timed = cfg.prof && cfg.prof->on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-    // the warp-per-variable kernel on a side stream when both have work (disjoint variables)
-    const bool fork = b.work_total > 0 && b.wide_total > 0 && can_fork(cfg);
-    cudaStream_t ws = s;
-    if (fork) {
-        cudaEventRecord(cfg.side->fork, s);
-        cudaStreamWaitEvent(cfg.side->s[0], cfg.side->fork, 0);
-        ws = cfg.side->s[0];
-    }
-    if (b.wide_total > 0) {
-        FlatArgs fa = flat(b, b.wide_prefix, b.wide_total);
-        void* args[] = {&fa};
-        const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_wide_kernel),
-                                              (b.wide_total + 7) / 8, 256, args, 0, ws, L2Window());
-        if (e != cudaSuccess) return e;
-        cfg.count();
-    }
-    if (b.work_total > 0) {
-        FlatArgs fa = flat(b, b.work_prefix, b.work_total);
-        void* args[] = {&fa};
-        const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_kernel),
-                                              (b.work_total + 255) / 256, 256, args, 0, s, L2Window());
-        if (e != cudaSuccess) return e;
-        cfg.count();
-    }
-    if (fork) {
-        cudaEventRecord(cfg.side->join[0], ws);
-        cudaStreamWaitEvent(s, cfg.side->join[0], 0);
-    }
+    FlatArgs work = flat(b, b.work_prefix, b.work_total);
+    FlatArgs wide = flat(b, b.wide_prefix, b.wide_total);
+    LbArgs la{b.insts, b.chunk_prefix, b.n_inst, kLbStage};
+    int nc = chunks;
+    int wide_blocks = (b.wide_total + 7) / 8;  // 8 warps per block
+    void* args[] = {&work, &wide, &la, &nc, &wide_blocks};
+    const int blocks = chunks + wide_blocks + (b.work_total + 255) / 256;
+    const void* fn = end ? reinterpret_cast<const void*>(deferred_sum_kernel<true>)
+                         : reinterpret_cast<const void*>(deferred_sum_kernel<false>);
+    const cudaError_t e = launch_windowed(fn, blocks, 256, args, 0, s, L2Window());
+    cfg.count();
     if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(1, ev0, ev1); }
-    return cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
+    return launch_deferred(b, false, cfg, s);
 }
 
 cudaEvent_t Profiler::take() {
@@ -619,21 +607,6 @@ void Profiler::release() {
     minor.clear();
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
     pool.clear();
-}
-
-cudaError_t launch_reduce_T_lb(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s) {
-    const bool timed = cfg.prof && cfg.prof->on;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (timed) { ev0 = cfg.prof->take(); ev1 = cfg.prof->take(); cudaEventRecord(ev0, s); }
-    FlatArgs fa = flat(b, b.work_prefix, b.work_total);
-    LbArgs la{b.insts, b.chunk_prefix, b.n_inst, kLbStage};
-    int chunks = b.chunks_total;
-    void* args[] = {&fa, &la, &chunks};
-    const cudaError_t e = launch_windowed(reinterpret_cast<const void*>(reduce_T_lb_kernel),
-                                          chunks + (b.work_total + 255) / 256, 256, args, 0, s, L2Window());
-    cfg.count();
-    if (timed) { cudaEventRecord(ev1, s); cfg.prof->record(1, ev0, ev1); }
-    return e;
 }
 
 cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s) {
@@ -735,22 +708,8 @@ cudaError_t launch_iteration(const DevBatch& b, const LaunchCfg& cfg, cudaStream
     if ((e = launch_sweep(b, kFwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
     if ((e = launch_sweep(b, kBwdUpdate, 0, cfg, s)) != cudaSuccess) return e;
-    // the bound reduction and the deferred sums both read only the pass's output
-    // (tile partials, multipliers) and write disjoint state: one launch when there
-    // are no warp-per-variable sums, else side by side on two streams
-    if (b.chunks_total > 0 && b.work_total > 0 && b.wide_total == 0) return launch_reduce_T_lb(b, cfg, s);
-    const bool fork = can_fork(cfg) && b.chunks_total > 0;
-    if (fork) {
-        if ((e = cudaEventRecord(cfg.side->fork, s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(cfg.side->s[1], cfg.side->fork, 0)) != cudaSuccess) return e;
-    }
-    if ((e = launch_lb_reduce(b, kLbStage, cfg, fork ? cfg.side->s[1] : s)) != cudaSuccess) return e;
-    if ((e = launch_reduce_T(b, cfg, s)) != cudaSuccess) return e;
-    if (fork) {
-        if ((e = cudaEventRecord(cfg.side->join[1], cfg.side->s[1])) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(s, cfg.side->join[1], 0)) != cudaSuccess) return e;
-    }
-    return launch_lb_commit(b, cfg, s);
+    // deferred sums, bound and the commit of the iteration: one launch
+    return launch_deferred(b, true, cfg, s);
 }
 
 }  // namespace fdog

@@ -136,9 +136,6 @@ int smem_max_layers(int width);
 cudaError_t launch_sweep(const DevBatch& b, int mode, int mm_flags, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_reduce_T(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_lb_reduce(const DevBatch& b, int target, const LaunchCfg& cfg, cudaStream_t s);
-// the end of an iteration in one launch (views without warp-per-variable sums): the descending
-// pass's deferred sums, its bound and the commit of the iteration
-cudaError_t launch_reduce_T_lb(const DevBatch& b, const LaunchCfg& cfg, cudaStream_t s);
 // FP64 evaluation of every member's bound sum_j E^j at lambda (or lambda + T
 // with add_t) into InstCtl::lb_eval (eval.cu)
 cudaError_t launch_eval64(const DevBatch& b, bool add_t, const LaunchCfg& cfg, cudaStream_t s);

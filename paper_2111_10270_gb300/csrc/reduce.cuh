@@ -29,10 +29,10 @@ struct FlatArgs {
 // its multiplier gathers are issued together.
 // one listed variable with at most 8 copies (work index g of the flat batch).
 // Instances whose stopping rule or iteration limit has stopped them are left
-// alone.  SNAPSHOT: the activity test reads InstCtl::pass_active, which the
-// ascending pass's deferred sums recorded (work index 0 of each instance),
-// instead of the control block's live state, which the end-of-iteration
-// kernel's commit may change while this runs.
+// alone.  Without SNAPSHOT the test reads the control block and work index 0
+// of each instance records its outcome in InstCtl::pass_active; with SNAPSHOT
+// it reads that record instead of the control block's live state, which the
+// end-of-iteration kernel's commit may change while this runs.
 template <bool SNAPSHOT = false>
 __device__ __forceinline__ void reduce_T_one(const FlatArgs& a, int g) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
@@ -162,11 +162,21 @@ __device__ __forceinline__ void commit_iteration(InstCtl* ctl, double lb) {
 // Variables with more than 8 copies (one assignment variable of a matching
 // problem can sit in hundreds of rows): one warp per variable g, lane l
 // summing copies l, l + 32, ... in ascending order, then a fixed butterfly.
+// SNAPSHOT as in reduce_T_one (the first such variable of an instance records
+// the activity when it is off).
+template <bool SNAPSHOT = false>
 __device__ __forceinline__ void reduce_T_wide_one(const FlatArgs& a, int g, int lane) {
     const int ii = find_inst(a.prefix, a.n_inst, g);
     const InstDev* __restrict__ I = a.insts + ii;
-    if (FDOG_INACTIVE(I->ctl)) return;
-    const int i = __ldcs(I->work + I->wb_start[FDOG_WBUCKETS - 1] + (g - __ldg(a.prefix + ii)));
+    const int w = g - __ldg(a.prefix + ii);
+    if (SNAPSHOT) {
+        if (!I->ctl->pass_active) return;
+    } else {
+        const bool inactive = FDOG_INACTIVE(I->ctl);
+        if (w == 0 && lane == 0) I->ctl->pass_active = inactive ? 0 : 1;
+        if (inactive) return;
+    }
+    const int i = __ldcs(I->work + I->wb_start[FDOG_WBUCKETS - 1] + w);
     const int b = I->csr_off[i], cnt = I->csr_off[i + 1] - b;
     const int32_t* __restrict__ pos = I->csr_pos + b;
     const float* __restrict__ lam = I->lam;

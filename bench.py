@@ -784,22 +784,34 @@ def main():
         t0 = time.perf_counter()
         e_arcs, h2d, d2h = 0.0, 0, 0
         plan_dev, plan_s = [], []
+        phases = {"create": 0.0, "build": 0.0, "solve": 0.0, "close": 0.0}
         for _ in range(args.e2e_steps):
-            e_inst = P.Instance.from_ilp(g, params).build(dev, stream)
+            # host clock per call: each call below returns with its device work done
+            # (build and the solve's read-back synchronise), so the phases add up
+            t1 = time.perf_counter()
+            e_inst = P.Instance.from_ilp(g, params)
+            t2 = time.perf_counter()
+            e_inst.build(dev, stream)
+            t3 = time.perf_counter()
             od, ps = e_inst.plan_stats()
             plan_dev.append(od)
             plan_s.append(ps)
             r = solve(e_inst, w["max_iters"], kr, args.dual_only)
+            t4 = time.perf_counter()
             hb, db = e_inst.transfer_bytes()
             h2d += hb
             d2h += db
             e_arcs += 4.0 * nodes * r["dual_iters"]
             e_inst.close()
+            t5 = time.perf_counter()
+            for k, a, b in (("create", t1, t2), ("build", t2, t3), ("solve", t3, t4), ("close", t4, t5)):
+                phases[k] += (b - a) * 1e3 / args.e2e_steps
         torch.cuda.synchronize()
         e_t = time.perf_counter() - t0
         e2e = {"value": e_arcs / e_t, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps,
                "planned_on_device": all(plan_dev), "plan_s": float(np.median(plan_s)),
+               "phases_ms_per_step": phases,
                "scope": "fdog_create from host CSR + upload of the rows + BDD construction and layout on the "
                         "device + solve + solution read-back"}
 

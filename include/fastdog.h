@@ -263,6 +263,16 @@ int fdog_build_bdds(fdog_instance* inst, int32_t device, void* cuda_stream);
 int fdog_release(fdog_instance* inst);
 
 /*
+ * Host memory (no counterpart in the paper).  Large host arrays that
+ * instances free (their copies of the ILP, host plans) are kept in a
+ * process-wide cache, at most 2 GiB, and reused by later instances of the
+ * same sizes, whose pages are then already mapped.  This call frees every
+ * cached buffer; *bytes_freed (may be NULL) receives their total size.
+ * Thread-safe; buffers in use by live instances are not affected.
+ */
+int fdog_host_cache_release(int64_t* bytes_freed);
+
+/*
  * Re-initialise the dual state on the device: lambda^j_i = c_i / |J_i|,
  * M-bar = 0, iteration counter and stopping history cleared (Alg. 1
  * initialisation).  The decomposition stays resident.

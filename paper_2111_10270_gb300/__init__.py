@@ -8,5 +8,6 @@ library raises.
 """
 from .capi import (  # noqa: F401
     FDOG_ECUDA, FDOG_EINFEASIBLE, FDOG_EINVAL, FDOG_ENOCONVERGE, FDOG_ENOMEM, FDOG_EQ, FDOG_ESTATE, FDOG_ETIMEOUT,
-    FDOG_EUNSUPPORTED, FDOG_GE, FDOG_LE, FDOG_OK, Batch, FdogError, Instance, Params, Server, lib, library_path,
+    FDOG_EUNSUPPORTED, FDOG_GE, FDOG_LE, FDOG_OK, Batch, FdogError, Instance, Params, Server, host_cache_release, lib,
+    library_path,
 )

@@ -17,7 +17,7 @@ LIB = os.path.join(BUILD, "libfastdog.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["bdd_build.cpp", "jit.cpp", "kernels.cu", "sweep_w2.cu", "sweep_w4.cu", "sweep_w8.cu", "sweep_w16.cu",
-           "engine.cu", "batch.cu", "server.cu", "api.cu", "state.cu", "noalloc.cu", "eval.cu", "shard.cu", "persist.cu", "serial.cu", "plan_device.cu", "split.cpp"]
+           "engine.cu", "batch.cu", "server.cu", "api.cu", "state.cu", "noalloc.cu", "eval.cu", "shard.cu", "persist.cu", "serial.cu", "plan_device.cu", "split.cpp", "host_pool.cpp"]
 GEN = os.path.join(BUILD, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

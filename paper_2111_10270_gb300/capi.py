@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
 _P = ctypes.c_void_p
 _i32, _i64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 SIGNATURES = {
+    "fdog_host_cache_release": (ctypes.c_int, [ctypes.POINTER(_i64)]),
     "fdog_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
     "fdog_create": (ctypes.c_int, [_i32, _P, _i32, _P, _P, _P, _P, _P, ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "fdog_plan": (ctypes.c_int, [_P, ctypes.POINTER(_i64)]),
@@ -195,6 +196,15 @@ def shard_plan(n_vars, row_ptr, col, coef, n_shards: int):
     if rc != FDOG_OK:
         raise FdogError(rc, "fdog_shard_plan")
     return row_shard[:n_rows], copies[:n_vars], shared[:n_vars]
+
+
+def host_cache_release() -> int:
+    """fdog_host_cache_release: frees the cached large host buffers, returns their bytes."""
+    b = _i64()
+    rc = lib().fdog_host_cache_release(ctypes.byref(b))
+    if rc != FDOG_OK:
+        raise FdogError(rc, "fdog_host_cache_release")
+    return b.value
 
 
 def default_params(**kw) -> Params:

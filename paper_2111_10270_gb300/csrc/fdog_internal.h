@@ -241,9 +241,21 @@ struct Decomposition {
     int32_t* d_bdd_row = nullptr;
 };
 
+// Process-wide cache of large host buffers (host_pool.cpp).  A buffer of at
+// least kHostPoolMin bytes that an instance frees is kept (up to a total of
+// kHostPoolCap bytes) and handed to the next request of the same rounded
+// size, whose pages are then already mapped: creating an instance of the
+// same size again costs its copy, not the page faults of fresh memory.
+constexpr size_t kHostPoolMin = size_t(1) << 20;
+constexpr size_t kHostPoolCap = size_t(2) << 30;
+void* host_pool_get(size_t bytes);  // throws std::bad_alloc
+void host_pool_put(void* p, size_t bytes) noexcept;
+size_t host_pool_release() noexcept;  // frees every cached buffer, returns the bytes
+
 // std::allocator whose value-less construct leaves trivial types
 // uninitialised: resize() then costs no fill pass over arrays that are
-// written right after (the instance's copy of the ILP).
+// written right after (the instance's copy of the ILP); large buffers come
+// from the host buffer cache.
 template <class T>
 struct DefaultInitAlloc : std::allocator<T> {
     template <class U>
@@ -253,6 +265,14 @@ struct DefaultInitAlloc : std::allocator<T> {
     DefaultInitAlloc() = default;
     template <class U>
     DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+    T* allocate(size_t n) {
+        if (n * sizeof(T) >= kHostPoolMin) return static_cast<T*>(host_pool_get(n * sizeof(T)));
+        return std::allocator<T>::allocate(n);
+    }
+    void deallocate(T* p, size_t n) noexcept {
+        if (n * sizeof(T) >= kHostPoolMin) host_pool_put(p, n * sizeof(T));
+        else std::allocator<T>::deallocate(p, n);
+    }
     template <class U>
     void construct(U* p) noexcept {
         ::new (static_cast<void*>(p)) U;

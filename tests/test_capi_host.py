@@ -245,3 +245,27 @@ def test_plan_digest_and_stats_on_host_plans(P):
     with pytest.raises(P.FdogError) as e:
         P.Instance.from_ilp(g).plan_digest()
     assert e.value.code == P.FDOG_ESTATE
+
+
+def test_host_cache_reuses_and_releases_buffers(P):
+    """Large host arrays that an instance frees are kept for the next instance
+    of the same sizes; fdog_host_cache_release frees them and reports their
+    bytes.  Instances built on reused buffers hold their own ILP exactly."""
+    P.host_cache_release()
+    g = ilpgen.mrf_grid(200, 200, 4, 3)
+    nnz = int(g.row_ptr[-1])
+    assert 4 * nnz >= 1 << 20  # the column and coefficient copies are large enough to be cached
+    a = P.Instance.from_ilp(g)
+    a.plan()
+    da = a.plan_digest()
+    a.close()
+    kept = P.host_cache_release()
+    assert kept >= 2 * 4 * nnz
+    assert P.host_cache_release() == 0
+    b = P.Instance.from_ilp(g)
+    b.close()
+    c = P.Instance.from_ilp(g)  # built on the buffers b left behind
+    c.plan()
+    assert list(c.plan_digest()) == list(da)
+    c.close()
+    assert P.host_cache_release() >= 2 * 4 * nnz

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) deferred_sum_kernel(FlatArgs work, FlatAr
 // End of an iteration for every member whose bound was staged: ring, counter
 // and the stopping test.  Runs after the deferred sums of the backward pass,
 // which must still see the iteration as active (the shards of a split
-// instance; whole instances commit inside deferred_sum_kernel<true>).
+// instance and the serial update of Eq. 4; the parallel update commits
+// inside deferred_sum_kernel<true>).
 __global__ void lb_commit_kernel(const InstDev* insts, int n) {
     dev::pdl_trigger();
     dev::pdl_wait();

@@ -241,9 +241,12 @@ int fdog_server_create(int32_t device, int64_t hbm_budget, int32_t max_active, i
     e.cfg.num_sms = prop.multiProcessorCount;
     // the server's views change with every admission, so they are not autotuned: 4 warps per block and
     // a block per group of tiles, which served the mixed MRF / matching stream 9% faster than one
-    // persistent wave (96 against 88 instances/s; 2 and 8 warps per block within 1%)
+    // persistent wave (96 against 88 instances/s; 2 and 8 warps per block within 1%); 4 iterations per graph
+    // replay, so that members that stop move on to rounding sooner (97 instances/s against 94-97 with 8
+    // and 92-94 with 16)
     e.cfg.warps_per_block = 4;
     e.cfg.max_waves = 0;
+    e.chunk = 4;
     e.cfg.prof = &s->prof;
     e.prof = nullptr;
     engine_use_side(e);

@@ -524,6 +524,26 @@ def test_early_stopping_rule(P, oracle_mod):
     assert inst.multipliers()[2].tobytes() == lam1 and inst.lower_bound() == lb1
 
 
+def test_stopped_instance_with_warp_per_variable_sums_stays_put(P):
+    """A matching instance has variables with more than 8 copies (the
+    warp-per-variable deferred sums, which share a launch with the bound and
+    the commit).  Once its stopping rule fires, further iterations in the same
+    graph replay and later calls change neither multipliers nor bound,
+    before and after the add-back."""
+    g = ilpgen.qap(5, 30, 60, 8, 4, sparse=True)
+    inst = gpu_instance(P, g, tol=1e-3, window=5, min_iters=10)
+    assert inst.info()["n_slots"] > 0
+    n, _ = inst.iterate(3000)
+    assert 10 <= n < 3000
+    lam0, lb0 = inst.multipliers()[2].tobytes(), inst.lower_bound()
+    assert inst.iterate(64)[0] == 0
+    assert inst.multipliers()[2].tobytes() == lam0 and inst.lower_bound() == lb0
+    inst.finalize()
+    lam1, lb1 = inst.multipliers()[2].tobytes(), inst.lower_bound()
+    assert inst.iterate(64)[0] == 0
+    assert inst.multipliers()[2].tobytes() == lam1 and inst.lower_bound() == lb1
+
+
 # ----------------------------------------------------------------------------
 # full-size workload (512 x 512 grid, 4 labels) in the benchmark's launch configuration
 # ----------------------------------------------------------------------------
